@@ -1,0 +1,350 @@
+"""Benchmark: HMC trajectories/s of the honeycomb-Hubbard hot path on GB300.
+
+One step = one HMC trajectory (heat bath, chi = M rho, n_md + 1 CG solves
+with forces, leapfrog, Metropolis) of the chosen workload, run by
+hmc_trajectory as one persistent launch.  Default workload: L=6 (72 sites),
+Nt=32, U=3.5, beta=4, 20 leapfrog steps over tau=1, thermalised from a cold
+start by untimed trajectories.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                    [--precision fp64|mixed] [--impl ours|reference]
+
+N > 1 (torchrun): each rank advances its own chain (chain id = rank): weak
+scaling, no collective on the data path.  Prints one JSON line on rank 0.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("HMC trajectories/s and M-applications/s (frac. of roofline), "
+          "mixed vs FP64 at equal tol")
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="l6_nt32")
+    ap.add_argument("--precision", default=None, choices=[None, "fp64", "mixed"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--therm", type=int, default=None,
+                    help="untimed thermalisation trajectories before warm-up")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-s", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return dict(FALLBACK), "fallback"
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- helpers
+def workload_params(name, precision):
+    from paper_2210_06874_gb300 import hmc, synth
+    w = dict(synth.WORKLOADS[name])
+    prec = precision or w["precision"]
+    p = hmc.Params(L=w["L"], Nt=w["Nt"], kappa=w["kappa"], U=w["U"], beta=w["beta"],
+                   n_md=w["n_md"], traj_length=w["traj_length"], cg_tol=w["cg_tol"],
+                   cg_max_iter=200000,
+                   precision=hmc.PREC_FP64 if prec == "fp64" else hmc.PREC_MIXED)
+    return w, p, prec
+
+
+def flops_per_apply(V, Nt):
+    """Algorithmic FLOPs of one M or M^dag application: the real V x V by
+    V x 2Nt contraction (4 V^2 Nt) plus phase, shift and subtraction
+    (~10 V Nt)."""
+    return 4.0 * V * V * Nt + 10.0 * V * Nt
+
+
+def applies_per_traj(out, n_md):
+    """M / M^dag applications in one trajectory: chi = M rho, two per CG
+    iteration, two per FP64 true-residual check (one per solve and one per
+    reliable update), one M^dag per force."""
+    return 1 + 2 * out.cg_iterations + 2 * (out.cg_solves + out.reliable_updates) + (n_md + 1)
+
+
+def measure_dgemm_tflops(torch):
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        a @ b
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = 1e30
+    for _ in range(5):
+        s.record()
+        a @ b
+        e.record()
+        e.synchronize()
+        best = min(best, s.elapsed_time(e))
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+
+
+def cpu_oracle_rate(name, prec, sample_s, phi_np=None):
+    """Time the CPU oracle (as it stands) on trajectories of the same workload
+    until about sample_s seconds of work are done."""
+    import numpy as np
+    from oracle import hmc as ohmc, lattice, operators as ops
+    from paper_2210_06874_gb300 import synth
+    w = synth.WORKLOADS[name]
+    delta = w["beta"] / w["Nt"]
+    E = ops.transfer_matrix(lattice.hopping_matrix(w["L"]), delta * w["kappa"])
+    phi = synth.start_field(name) if phi_np is None else phi_np
+    t0 = time.perf_counter()
+    n = 0
+    iters = 0
+    while True:
+        out = ohmc.trajectory(E, phi, delta, w["U"], w["traj_length"] / w["n_md"], w["n_md"],
+                              w["seed"], 10_000 + n, 0, tol=w["cg_tol"], max_iter=200000)
+        phi = out["phi"]
+        iters += out["cg_iters"]
+        n += 1
+        if time.perf_counter() - t0 > sample_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "trajectories/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": "%d oracle trajectories of %s (%d CG iterations), %.1f s; NumPy FP64, "
+                      "BLAS threads as configured" % (n, name, iters, dt)}
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    from paper_2210_06874_gb300 import synth
+    name = args.workload
+    w = synth.WORKLOADS[name]
+    prec = args.precision or w["precision"]
+    rates = []
+    for k in range(args.warmup + args.steps):
+        r = cpu_oracle_rate(name, prec, min(args.cpu_sample_s, 20.0))
+        if k >= args.warmup:
+            rates.append(r["value"])
+    value = statistics.mean(rates)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "trajectories/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": name, "precision": "fp64 (oracle)", "L": w["L"], "Nt": w["Nt"],
+                   "n_md": w["n_md"]},
+        "cpu_baseline": {"value": value, "unit": "trajectories/s", "cores": os.cpu_count(),
+                         "kind": "oracle",
+                         "sample": "each step: oracle trajectories of %s for ~%.0f s"
+                                   % (name, min(args.cpu_sample_s, 20.0))},
+        "e2e": {"value": value, "unit": "trajectories/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2210_06874_gb300 import build_lib, hmc, synth
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    build_lib.build()
+    name = args.workload
+    w, params, prec = workload_params(name, args.precision)
+    ctx = hmc.Context(params)
+    V, Nt = params.V, params.Nt
+    dev = torch.device("cuda", local_rank)
+    phi = torch.from_numpy(synth.start_field(name)).to(dev)
+    seed = w["seed"]
+    n_therm = args.therm if args.therm is not None else (0 if w["start"] == "gaussian" else 20)
+    traj = 0
+    for _ in range(n_therm + args.warmup):
+        ctx.trajectory(phi, seed, traj, rank, allow_not_converged=True)
+        traj += 1
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    total_ms, outs = 0.0, []
+    for _ in range(args.steps):
+        flush.fill_(1.0)                       # evict L2 between timed trajectories
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        out = ctx.trajectory(phi, seed, traj, rank, allow_not_converged=True)
+        e.record(stream)
+        e.synchronize()
+        total_ms += s.elapsed_time(e)
+        outs.append(out)
+        traj += 1
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms * 1e-3)
+
+    # end to end through the public API with host buffers: pinned phi in,
+    # trajectory, phi and the trajectory record back to the host
+    phi_host = torch.empty((Nt, V), dtype=torch.float64, pin_memory=True)
+    phi_host.copy_(phi.cpu())
+    back = torch.empty_like(phi_host)
+    torch.cuda.synchronize()
+    e2e_steps = max(2, min(args.steps, 5))
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    for _ in range(e2e_steps):
+        phi.copy_(phi_host, non_blocking=True)
+        out = ctx.trajectory(phi, seed, traj, rank, allow_not_converged=True)
+        back.copy_(phi, non_blocking=True)
+        stream.synchronize()
+        phi_host.copy_(back)
+        traj += 1
+    e.record(stream)
+    e.synchronize()
+    e2e_ms = s.elapsed_time(e) / e2e_steps
+    h2d = Nt * V * 8
+    d2h = Nt * V * 8 + 8 * 16
+
+    # roofline of the dominant (only) kernel: the persistent trajectory launch
+    peaks, peaks_kind = load_peaks()
+    mean_iters = statistics.mean(o.cg_iterations for o in outs)
+    n_app = statistics.mean(applies_per_traj(o, params.n_md) for o in outs)
+    flop = n_app * flops_per_apply(V, Nt)
+    achieved = flop / (ms_per_step * 1e-3) / 1e12
+    if prec == "fp64":
+        peak = measure_dgemm_tflops(torch)
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "measured cuBLAS DGEMM 4096^3 on this GPU (FP64 ALU peak)"}
+    else:
+        peak = peaks.get("bf16_tflops_sustained", FALLBACK["bf16_tflops_sustained"])
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "%s bf16 dense sustained (fp16 has the same rate)" % peaks_kind}
+    line = {
+        "metric": METRIC, "value": value, "unit": "trajectories/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == "fp64" else "f16-split/f32 (f64 residuals)",
+        "data": "synthetic",
+        "config": {"workload": name, "precision": prec, "L": w["L"], "V": V, "Nt": Nt,
+                   "U": w["U"], "beta": w["beta"], "n_md": params.n_md,
+                   "cg_tol": params.cg_tol, "thermalisation_trajectories": n_therm,
+                   "l2": "flushed (256 MB write) between timed trajectories",
+                   "parallelism": "replicas (one chain per GPU)"},
+        "m_applications_per_s": world * n_app / (ms_per_step * 1e-3),
+        "cg_iterations_per_traj": mean_iters,
+        "acceptance": statistics.mean(o.accept for o in outs),
+        "max_true_residual": max(o.max_true_residual for o in outs),
+        "e2e": {"value": world / (e2e_ms * 1e-3), "unit": "trajectories/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps,
+        "roofline": roof,
+        "clocks": clk,
+        "wall_s_timed_region": wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_rate(name, prec, args.cpu_sample_s,
+                                               phi_np=phi.cpu().numpy())
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,170 @@
+/*
+ * hmc.h -- C ABI of the GB300 (sm_103a) library for the hot path of Hybrid
+ * Monte Carlo on the honeycomb Hubbard model (arXiv:2210.06874, §2).
+ *
+ * The operator.  Lattice: L x L unit cells of the honeycomb lattice, two
+ * sites each, V = 2 L^2 sites, periodic (§1, Fig. 1; §4).  With delta =
+ * beta / Nt, h the nearest-neighbour adjacency and E = exp(delta*kappa*h),
+ * the fermion matrix on space-time vectors psi[t][x] is
+ *
+ *     (M psi)_t     = psi_t - s_t     * E diag(exp(i phi_{t-1})) psi_{t-1}
+ *     (M^dag psi)_t = psi_t - s_{t+1} * diag(exp(-i phi_t)) E psi_{t+1}
+ *     s_0 = -1 (antiperiodic time boundary), s_t = +1 otherwise, t mod Nt
+ *
+ * i.e. the transfer-matrix (exponential-hopping) form of the fermion
+ * operator whose linear form is printed as Eq. (2.2).  phi is the phase
+ * angle: phi = delta * phi_paper, so the bosonic action of Eq. (2.1) reads
+ * sum(phi^2) / (2 delta U).
+ *
+ * Layouts (all arrays time-major, site index fastest):
+ *   phi, pi, F   double  [Nt][V]
+ *   complex128   double2 [Nt][V]   interleaved (re, im)  == torch.complex128
+ *   complex64    float2  [Nt][V]   interleaved (re, im)  == torch.complex64
+ *   site x = s*L*L + m1*L + m2 (s = 0: sublattice A, s = 1: sublattice B);
+ *   the A site of cell (m1,m2) bonds to the B sites of cells (m1,m2),
+ *   (m1-1,m2), (m1,m2-1), indices mod L.
+ *
+ * Ownership.  Every array pointer is caller-owned DEVICE memory (e.g. a
+ * torch tensor's data_ptr()) unless named *_host; the library never frees
+ * or retains it past the call.  hmc_ctx owns only derived data: E in FP64
+ * and its FP16 split, solver workspaces and the device status words.
+ * `stream` is a cudaStream_t (NULL = legacy default stream).  Calls that
+ * return results in host structs (stats, out) synchronise that stream;
+ * the others are asynchronous.  One context serves one stream at a time:
+ * its workspaces are shared by all calls on it.
+ *
+ * Errors.  Every entry point returns an hmc_status.  Argument checks happen
+ * on the host before any launch.  Device-side failures (non-finite
+ * reductions, solver not converged, a bounded wait that gave up) are
+ * recorded in a device status word and reported by the next synchronising
+ * call on the context.  No call traps or aborts the GPU context.
+ */
+#ifndef HMC_GB300_H
+#define HMC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum hmc_status {
+    HMC_OK = 0,
+    HMC_ERR_BAD_ARG = -1,           /* invalid size, pointer or parameter */
+    HMC_ERR_CUDA = -2,              /* a CUDA runtime call failed */
+    HMC_ERR_CG_NOT_CONVERGED = -3,  /* max_iter reached above tolerance */
+    HMC_ERR_NONFINITE = -4,         /* NaN/Inf seen in a reduction */
+    HMC_ERR_TIMEOUT = -5,           /* a bounded device wait gave up */
+    HMC_ERR_UNSUPPORTED = -6        /* sizes beyond what a kernel supports */
+} hmc_status;
+
+typedef enum hmc_precision {
+    HMC_PREC_FP64 = 0,   /* every step in FP64 on CUDA cores */
+    HMC_PREC_MIXED = 1   /* FP16-split tensor-core contraction, FP32 CG with
+                            FP64 reliable updates; FP64 for residuals, sums,
+                            force and Metropolis */
+} hmc_precision;
+
+/* Physics and solver parameters of one Markov chain. */
+typedef struct hmc_params {
+    int L;               /* unit cells per direction, 1 <= L; V = 2 L^2 */
+    int Nt;              /* time slices, >= 1 */
+    double kappa;        /* hopping amplitude of Eq. (1.1) */
+    double U;            /* on-site coupling of Eq. (1.1), > 0 */
+    double beta;         /* inverse temperature; delta = beta / Nt */
+    int n_md;            /* leapfrog steps per trajectory, >= 1 */
+    double traj_length;  /* trajectory length tau; eps = tau / n_md */
+    double cg_tol;       /* target |chi - M M^dag x| / |chi| (FP64 true residual) */
+    int cg_max_iter;     /* CG iteration cap per solve */
+    int precision;       /* hmc_precision used by hmc_trajectory */
+    double ru_delta;     /* mixed CG: reliable update when |r| < ru_delta * max|r|
+                            since the last update (0 selects 0.05) */
+} hmc_params;
+
+typedef struct hmc_cg_stats {
+    int iterations;          /* CG iterations (inner iterations for MIXED) */
+    int reliable_updates;    /* FP64 residual recomputations (MIXED) */
+    double true_residual;    /* |chi - M M^dag x| / |chi| in FP64 */
+    int status;              /* hmc_status of the solve */
+} hmc_cg_stats;
+
+typedef struct hmc_traj_out {
+    double dH;               /* H(end) - H(start), Eq. (2.1) */
+    double H0, H1;
+    double u;                /* Metropolis uniform drawn for this trajectory */
+    int accept;              /* 1 if u < exp(-dH) */
+    int cg_iterations;       /* summed over the n_md + 1 solves */
+    int cg_solves;
+    int reliable_updates;
+    double max_true_residual;
+    int status;
+} hmc_traj_out;
+
+typedef struct hmc_ctx hmc_ctx;
+
+/* Build h and E = exp(delta*kappa*h) (FP64, plus its FP16 hi/lo split for
+ * the MIXED path) for the lattice in *p and allocate workspaces on the
+ * current CUDA device.  *out receives the context.
+ * Errors: HMC_ERR_BAD_ARG (L < 1, Nt < 1, U <= 0, ...), HMC_ERR_CUDA. */
+int hmc_ctx_create(const hmc_params* p, hmc_ctx** out);
+
+/* Free everything the context owns.  NULL is accepted. */
+int hmc_ctx_destroy(hmc_ctx* ctx);
+
+/* Copy the FP64 transfer matrix E (V x V, row-major) to host memory. */
+int hmc_get_transfer_matrix(hmc_ctx* ctx, double* E_host, size_t n_elems);
+
+/* psi_out = M[phi] psi_in  (definition above; Eq. (2.2) in exponential
+ * form).  prec = HMC_PREC_FP64: psi_in/psi_out complex128; FP64 CUDA-core
+ * contraction.  prec = HMC_PREC_MIXED: psi_in/psi_out complex64; FP16-split
+ * tensor-core contraction with FP32 accumulation.  psi_out must not alias
+ * psi_in.  Asynchronous on `stream`. */
+int hmc_apply_M(hmc_ctx* ctx, const double* phi, const void* psi_in, void* psi_out,
+                int prec, void* stream);
+
+/* psi_out = M^dag[phi] psi_in; layouts and precision as hmc_apply_M. */
+int hmc_apply_Mdag(hmc_ctx* ctx, const double* phi, const void* psi_in, void* psi_out,
+                   int prec, void* stream);
+
+/* Solve (M M^dag) x = chi (Eq. (2.1)'s pseudofermion kernel) by conjugate
+ * gradients from x0 = 0.  chi and x are complex128 [Nt][V].  prec FP64:
+ * plain CG, stop on the recursive residual.  prec MIXED: FP32 CG on the
+ * tensor-core operator with FP64 reliable updates; stops on the FP64 true
+ * residual.  Both report the final FP64 true residual in *stats (host
+ * struct; the call synchronises `stream`).  Returns
+ * HMC_ERR_CG_NOT_CONVERGED if max_iter was hit (x holds the last iterate). */
+int hmc_cg_solve(hmc_ctx* ctx, const double* phi, const void* chi, void* x,
+                 double tol, int max_iter, int prec, hmc_cg_stats* stats, void* stream);
+
+/* F = dS/dphi for S = sum(phi^2)/(2 delta U) + chi^dag (M M^dag)^{-1} chi,
+ * given the kept solve x = (M M^dag)^{-1} chi (complex128):
+ *     F = phi / (delta U) + 2 Im(x * conj(M^dag x))    (FP64).
+ * Asynchronous. */
+int hmc_force(hmc_ctx* ctx, const double* phi, const void* x, double* F, void* stream);
+
+/* One HMC trajectory (§2) on device field phi (in/out, double [Nt][V]):
+ * momenta pi ~ exp(-pi^2/2) and noise rho ~ exp(-rho^dag rho) from Philox
+ * streams (seed, traj_index, chain), chi = M rho, leapfrog of n_md steps
+ * (drift phi += eps*delta*pi, kick pi -= eps*delta*dS/dphi), Metropolis
+ * with u from the generator.  On rejection phi is restored.  The whole
+ * trajectory runs in one persistent launch; *out (host) is filled and the
+ * stream synchronised.  Precision: params.precision. */
+int hmc_trajectory(hmc_ctx* ctx, double* phi, uint64_t seed, uint64_t traj_index,
+                   uint32_t chain, hmc_traj_out* out, void* stream);
+
+/* Philox4x32-10 draws of the library's streams, for checking the generator
+ * (Salmon et al., SC'11): element e of stream `stream_id` for
+ * (seed, traj, chain) -> raw[4e..4e+3] (uint32, may be NULL) and the
+ * Box-Muller pair z0[e], z1[e] (double, may be NULL).  Device pointers;
+ * n >= 0 elements.  Asynchronous. */
+int hmc_rng_draw(uint64_t seed, uint32_t stream_id, uint64_t traj, uint32_t chain,
+                 int64_t n, uint32_t* raw, double* z0, double* z1, void* stream);
+
+/* Library version string (static storage). */
+const char* hmc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HMC_GB300_H */

@@ -1,0 +1,46 @@
+// ctx.h -- the opaque hmc_ctx and the per-chain device view handed to kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hmc.h"
+
+namespace hmc {
+
+// Device view of one chain: sizes, constants and the workspaces the
+// persistent kernels use.  Passed by value to kernels.
+struct ChainView {
+    int L, V, Nt, N;            // N = V * Nt
+    double delta, kappa, U;
+    const double* E;            // V x V FP64, row-major, exactly symmetric
+    // FP16 split of E for the tensor-core path (row-major, padded):
+    //   E ~= (E_hi + E_lo * 2^-kLoShift) with rows and cols padded to Vp.
+    const void* E_hi;           // __half [Vr][Vp]
+    const void* E_lo;           // __half [Vr][Vp]
+    int Vr, Vp;                 // padded rows (multiple of 128), cols (multiple of 64)
+    // FP64 workspaces, double2 [Nt][V] each
+    double2 *cis;               // exp(i phi)
+    double2 *x, *r, *p, *q, *chi, *rho;
+    double *pi, *phi_old;       // double [Nt][V]
+    // FP32 workspaces for the mixed path, float2 [Nt][V] each
+    float2 *cis_f, *r_f, *p_f, *q_f, *x_f;
+    // team synchronisation
+    unsigned* bar;              // 2 words
+    int* status;                // device status word
+    double* partials;           // kSlots * kMaxTeam * kVals
+    double* scalars;            // per-call scalar outputs (see kernels)
+};
+
+}  // namespace hmc
+
+struct hmc_ctx {
+    hmc_params params;
+    int device;
+    int num_sms;
+    hmc::ChainView view;
+    // owned device allocations (freed by hmc_ctx_destroy)
+    void* allocs[32];
+    int n_allocs;
+    double* scalars_host;       // pinned, mirrors view.scalars
+};

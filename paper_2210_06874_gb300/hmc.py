@@ -1,0 +1,253 @@
+"""ctypes binding of the C ABI in include/hmc.h (argument marshalling only).
+
+Every function here checks tensor shapes, dtypes and devices, passes raw
+device pointers and the current CUDA stream to libhmc_gb300.so and turns a
+non-zero hmc_status into HmcError.  No step of the method runs in Python:
+there is no CPU fallback, and importing this module on a machine without the
+built library raises.
+
+Field layouts (torch tensors on the context's CUDA device, contiguous):
+    phi, F, pi      float64  [Nt, V]
+    psi (FP64)      complex128 [Nt, V]
+    psi (MIXED)     complex64  [Nt, V]
+"""
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhmc_gb300.so")
+
+HMC_OK = 0
+HMC_ERR_BAD_ARG = -1
+HMC_ERR_CUDA = -2
+HMC_ERR_CG_NOT_CONVERGED = -3
+HMC_ERR_NONFINITE = -4
+HMC_ERR_TIMEOUT = -5
+HMC_ERR_UNSUPPORTED = -6
+STATUS_NAMES = {
+    0: "HMC_OK", -1: "HMC_ERR_BAD_ARG", -2: "HMC_ERR_CUDA", -3: "HMC_ERR_CG_NOT_CONVERGED",
+    -4: "HMC_ERR_NONFINITE", -5: "HMC_ERR_TIMEOUT", -6: "HMC_ERR_UNSUPPORTED",
+}
+PREC_FP64 = 0
+PREC_MIXED = 1
+
+
+class HmcError(RuntimeError):
+    def __init__(self, fn, code):
+        super().__init__("%s failed: %s (%d)" % (fn, STATUS_NAMES.get(code, "?"), code))
+        self.code = code
+
+
+class hmc_params(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("Nt", ctypes.c_int), ("kappa", ctypes.c_double),
+                ("U", ctypes.c_double), ("beta", ctypes.c_double), ("n_md", ctypes.c_int),
+                ("traj_length", ctypes.c_double), ("cg_tol", ctypes.c_double),
+                ("cg_max_iter", ctypes.c_int), ("precision", ctypes.c_int),
+                ("ru_delta", ctypes.c_double)]
+
+
+class hmc_cg_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("reliable_updates", ctypes.c_int),
+                ("true_residual", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+class hmc_traj_out(ctypes.Structure):
+    _fields_ = [("dH", ctypes.c_double), ("H0", ctypes.c_double), ("H1", ctypes.c_double),
+                ("u", ctypes.c_double), ("accept", ctypes.c_int),
+                ("cg_iterations", ctypes.c_int), ("cg_solves", ctypes.c_int),
+                ("reliable_updates", ctypes.c_int), ("max_true_residual", ctypes.c_double),
+                ("status", ctypes.c_int)]
+
+
+_lib = None
+
+# symbol -> (restype, argtypes); mirrors include/hmc.h
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "hmc_ctx_create": (ctypes.c_int, [ctypes.POINTER(hmc_params), ctypes.POINTER(_P)]),
+    "hmc_ctx_destroy": (ctypes.c_int, [_P]),
+    "hmc_get_transfer_matrix": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    "hmc_apply_M": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, _P]),
+    "hmc_apply_Mdag": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, _P]),
+    "hmc_cg_solve": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_double, ctypes.c_int,
+                                    ctypes.c_int, ctypes.POINTER(hmc_cg_stats), _P]),
+    "hmc_force": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "hmc_trajectory": (ctypes.c_int, [_P, _P, ctypes.c_uint64, ctypes.c_uint64,
+                                      ctypes.c_uint32, ctypes.POINTER(hmc_traj_out), _P]),
+    "hmc_rng_draw": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
+                                    ctypes.c_uint32, ctypes.c_int64, _P, _P, _P, _P]),
+    "hmc_version": (ctypes.c_char_p, []),
+}
+
+
+def load_library(path=LIB_PATH):
+    """Load libhmc_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libhmc_gb300.so is missing at %s: run "
+                           "`python -m paper_2210_06874_gb300.build_lib` first" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(fn, code, allow=()):
+    if code != HMC_OK and code not in allow:
+        raise HmcError(fn, code)
+    return code
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+@dataclass
+class Params:
+    L: int
+    Nt: int
+    kappa: float = 1.0
+    U: float = 2.0
+    beta: float = 2.0
+    n_md: int = 10
+    traj_length: float = 1.0
+    cg_tol: float = 1e-12
+    cg_max_iter: int = 100000
+    precision: int = PREC_FP64
+    ru_delta: float = 0.0
+
+    @property
+    def V(self):
+        return 2 * self.L * self.L
+
+    @property
+    def delta(self):
+        return self.beta / self.Nt
+
+    def to_c(self):
+        return hmc_params(self.L, self.Nt, self.kappa, self.U, self.beta, self.n_md,
+                          self.traj_length, self.cg_tol, self.cg_max_iter, self.precision,
+                          self.ru_delta)
+
+
+class Context:
+    """Owns an hmc_ctx (E, its FP16 split, workspaces) on the current device."""
+
+    def __init__(self, params: Params):
+        self.lib = load_library()
+        self.params = params
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        h = ctypes.c_void_p()
+        cp = params.to_c()
+        _check("hmc_ctx_create", self.lib.hmc_ctx_create(ctypes.byref(cp), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self.lib.hmc_ctx_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- checks ------------------------------------------------------------
+    @property
+    def shape(self):
+        return (self.params.Nt, self.params.V)
+
+    def _field(self, t, name, dtype):
+        if not isinstance(t, torch.Tensor) or t.device != self.device or t.dtype != dtype \
+                or tuple(t.shape) != self.shape or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous %s tensor of shape %s on %s"
+                             % (name, dtype, self.shape, self.device))
+        return t
+
+    # -- entry points --------------------------------------------------------
+    def transfer_matrix(self):
+        V = self.params.V
+        out = torch.empty((V, V), dtype=torch.float64)
+        _check("hmc_get_transfer_matrix",
+               self.lib.hmc_get_transfer_matrix(self._h, _ptr(out), V * V))
+        return out
+
+    def _apply(self, fn, phi, psi, out, prec):
+        dt = torch.complex128 if prec == PREC_FP64 else torch.complex64
+        self._field(phi, "phi", torch.float64)
+        self._field(psi, "psi", dt)
+        if out is None:
+            out = torch.empty_like(psi)
+        self._field(out, "out", dt)
+        _check(fn, getattr(self.lib, fn)(self._h, _ptr(phi), _ptr(psi), _ptr(out), prec,
+                                         _stream()))
+        return out
+
+    def apply_M(self, phi, psi, out=None, prec=PREC_FP64):
+        return self._apply("hmc_apply_M", phi, psi, out, prec)
+
+    def apply_Mdag(self, phi, psi, out=None, prec=PREC_FP64):
+        return self._apply("hmc_apply_Mdag", phi, psi, out, prec)
+
+    def cg_solve(self, phi, chi, tol=None, max_iter=None, prec=PREC_FP64, x=None,
+                 allow_not_converged=False):
+        self._field(phi, "phi", torch.float64)
+        self._field(chi, "chi", torch.complex128)
+        if x is None:
+            x = torch.empty_like(chi)
+        self._field(x, "x", torch.complex128)
+        st = hmc_cg_stats()
+        tol = self.params.cg_tol if tol is None else tol
+        max_iter = self.params.cg_max_iter if max_iter is None else max_iter
+        allow = (HMC_ERR_CG_NOT_CONVERGED,) if allow_not_converged else ()
+        _check("hmc_cg_solve", self.lib.hmc_cg_solve(self._h, _ptr(phi), _ptr(chi), _ptr(x),
+                                                     tol, max_iter, prec, ctypes.byref(st),
+                                                     _stream()), allow)
+        return x, st
+
+    def force(self, phi, x, F=None):
+        self._field(phi, "phi", torch.float64)
+        self._field(x, "x", torch.complex128)
+        if F is None:
+            F = torch.empty_like(phi)
+        self._field(F, "F", torch.float64)
+        _check("hmc_force", self.lib.hmc_force(self._h, _ptr(phi), _ptr(x), _ptr(F), _stream()))
+        return F
+
+    def trajectory(self, phi, seed, traj_index, chain=0, allow_not_converged=False):
+        self._field(phi, "phi", torch.float64)
+        out = hmc_traj_out()
+        allow = (HMC_ERR_CG_NOT_CONVERGED,) if allow_not_converged else ()
+        _check("hmc_trajectory", self.lib.hmc_trajectory(self._h, _ptr(phi), seed, traj_index,
+                                                         chain, ctypes.byref(out), _stream()),
+               allow)
+        return out
+
+
+def rng_draw(seed, stream_id, traj, chain, n, device=None):
+    """Philox draws of the library's generator: (raw uint32 [n,4], z0, z1)."""
+    lib = load_library()
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    raw = torch.empty((n, 4), dtype=torch.int32, device=device)
+    z0 = torch.empty(n, dtype=torch.float64, device=device)
+    z1 = torch.empty(n, dtype=torch.float64, device=device)
+    _check("hmc_rng_draw", lib.hmc_rng_draw(seed, stream_id, traj, chain, n, _ptr(raw),
+                                            _ptr(z0), _ptr(z1), _stream()))
+    return raw, z0, z1
+
+
+def version():
+    return load_library().hmc_version().decode()

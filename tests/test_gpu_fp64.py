@@ -1,0 +1,182 @@
+"""GPU parity of the FP64 path against the FP64 oracle, through the C ABI.
+
+Tolerance: FP64-path results must match the oracle to 1e-10 relative
+(operator applications agree to ~1e-14; solves to the solver tolerance
+times the conditioning).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import hmc as ohmc, lattice, operators as ops, philox
+from paper_2210_06874_gb300 import hmc, synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def ctx_for(L, Nt, beta=2.0, U=2.0, kappa=1.0, **kw):
+    return hmc.Context(hmc.Params(L=L, Nt=Nt, beta=beta, U=U, kappa=kappa, **kw))
+
+
+def oracle_E(L, Nt, beta, kappa=1.0):
+    return ops.transfer_matrix(lattice.hopping_matrix(L), beta / Nt * kappa)
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def t64(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+@pytest.mark.parametrize("stream_id", [0, 1, 2, 5])
+def test_rng_matches_oracle(stream_id):
+    n = 4099
+    raw, z0, z1 = hmc.rng_draw(123456789012345, stream_id, 77, 3, n)
+    want = philox.philox4x32_10(np.arange(n), stream_id, 77, 3, 123456789012345 & 0xFFFFFFFF,
+                                123456789012345 >> 32)
+    got = raw.cpu().numpy().view(np.uint32).astype(np.uint64)
+    for j in range(4):
+        assert np.array_equal(got[:, j], want[j])
+    w0, w1 = philox.normal_pair(123456789012345, stream_id, 77, 3, n)
+    assert np.abs(z0.cpu().numpy() - w0).max() < 1e-13
+    assert np.abs(z1.cpu().numpy() - w1).max() < 1e-13
+
+
+@pytest.mark.parametrize("L,Nt,beta,kappa", [(1, 4, 1.0, 1.0), (2, 5, 2.0, 1.0),
+                                             (3, 8, 2.0, 1.0), (12, 64, 8.0, 1.0),
+                                             (24, 96, 12.0, 1.0), (4, 4, 2.0, -0.5)])
+def test_transfer_matrix_matches_oracle(L, Nt, beta, kappa):
+    c = ctx_for(L, Nt, beta=beta, kappa=kappa)
+    E = c.transfer_matrix().numpy()
+    assert np.abs(E - oracle_E(L, Nt, beta, kappa)).max() < 1e-14
+    assert np.array_equal(E, E.T)
+
+
+SIZES = [(1, 1), (1, 3), (2, 5), (3, 8), (5, 13), (6, 32), (7, 9), (12, 64)]
+
+
+@pytest.mark.parametrize("L,Nt", SIZES)
+def test_apply_M_and_Mdag_fp64(L, Nt):
+    beta, U = 0.125 * Nt, 3.0
+    V = 2 * L * L
+    c = ctx_for(L, Nt, beta=beta, U=U)
+    E = oracle_E(L, Nt, beta)
+    phi = synth.gaussian_field(L * 100 + Nt, Nt, V, beta / Nt * U)
+    psi = synth.complex_gaussian(L * 1000 + Nt, Nt, V)
+    got = c.apply_M(t64(phi), t64(psi)).cpu().numpy()
+    assert rel(got, ops.apply_M(E, phi, psi)) < 1e-13
+    got = c.apply_Mdag(t64(phi), t64(psi)).cpu().numpy()
+    assert rel(got, ops.apply_Mdag(E, phi, psi)) < 1e-13
+
+
+def test_apply_full_size_l24_nt96():
+    L, Nt, beta, U = 24, 96, 12.0, 4.0
+    V = 2 * L * L
+    c = ctx_for(L, Nt, beta=beta, U=U)
+    E = oracle_E(L, Nt, beta)
+    phi = synth.gaussian_field(5, Nt, V, beta / Nt * U)
+    psi = synth.complex_gaussian(6, Nt, V)
+    got = c.apply_M(t64(phi), t64(psi)).cpu().numpy()
+    want = ops.apply_M(E, phi, psi)
+    assert np.abs(got - want).max() < 1e-12 * np.abs(want).max()
+    got = c.apply_Mdag(t64(phi), t64(psi)).cpu().numpy()
+    want = ops.apply_Mdag(E, phi, psi)
+    assert np.abs(got - want).max() < 1e-12 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("L,Nt,beta,U", [(1, 2, 1.0, 2.0), (2, 6, 1.5, 3.0), (3, 8, 2.0, 2.0),
+                                         (6, 32, 4.0, 3.5)])
+def test_cg_fp64_matches_oracle(L, Nt, beta, U):
+    V = 2 * L * L
+    c = ctx_for(L, Nt, beta=beta, U=U)
+    E = oracle_E(L, Nt, beta)
+    phi = synth.gaussian_field(11, Nt, V, beta / Nt * U, scale=0.5)
+    chi = synth.complex_gaussian(12, Nt, V)
+    x, st = c.cg_solve(t64(phi), t64(chi), tol=1e-12)
+    want, it, _ = ohmc.cg_solve(E, phi, chi, tol=1e-14, max_iter=50000)
+    assert st.status == 0
+    assert st.true_residual < 1e-11
+    assert rel(x.cpu().numpy(), want) < 1e-10
+    _, it12, _ = ohmc.cg_solve(E, phi, chi, tol=1e-12, max_iter=50000)
+    assert abs(st.iterations - it12) <= 2
+
+
+def test_cg_reports_not_converged_and_nonfinite():
+    L, Nt = 3, 8
+    c = ctx_for(L, Nt)
+    phi = t64(synth.gaussian_field(1, Nt, 18, 0.5))
+    chi = t64(synth.complex_gaussian(2, Nt, 18))
+    with pytest.raises(hmc.HmcError) as e:
+        c.cg_solve(phi, chi, tol=1e-12, max_iter=1)
+    assert e.value.code == hmc.HMC_ERR_CG_NOT_CONVERGED
+    bad = phi.clone()
+    bad[3, 4] = float("nan")
+    with pytest.raises(hmc.HmcError) as e:
+        c.cg_solve(bad, chi, tol=1e-12)
+    assert e.value.code == hmc.HMC_ERR_NONFINITE
+    x, st = c.cg_solve(phi, chi, tol=1e-12)      # context still usable afterwards
+    assert st.status == 0
+
+
+@pytest.mark.parametrize("L,Nt", [(2, 5), (3, 8), (6, 32)])
+def test_force_fp64_matches_oracle(L, Nt):
+    beta, U = 0.125 * Nt, 3.5
+    V = 2 * L * L
+    c = ctx_for(L, Nt, beta=beta, U=U)
+    E = oracle_E(L, Nt, beta)
+    phi = synth.gaussian_field(21, Nt, V, beta / Nt * U, scale=0.5)
+    x = synth.complex_gaussian(22, Nt, V)
+    got = c.force(t64(phi), t64(x)).cpu().numpy()
+    want = ohmc.force_from_solution(E, phi, x, beta / Nt, U)
+    assert rel(got, want) < 1e-13
+
+
+def run_oracle_traj(w, phi, traj):
+    E = oracle_E(w["L"], w["Nt"], w["beta"])
+    delta = w["beta"] / w["Nt"]
+    return ohmc.trajectory(E, phi, delta, w["U"], w["traj_length"] / w["n_md"], w["n_md"],
+                           w["seed"], traj, 0, tol=w["cg_tol"])
+
+
+def test_trajectory_fp64_matches_oracle_l3_nt8():
+    w = synth.WORKLOADS["l3_nt8"]
+    c = hmc.Context(hmc.Params(L=w["L"], Nt=w["Nt"], kappa=w["kappa"], U=w["U"],
+                               beta=w["beta"], n_md=w["n_md"], traj_length=w["traj_length"],
+                               cg_tol=w["cg_tol"], precision=hmc.PREC_FP64))
+    phi_np = synth.start_field("l3_nt8") * 0.5
+    phi = t64(phi_np)
+    for traj in range(3):
+        want = run_oracle_traj(w, phi_np, traj)
+        out = c.trajectory(phi, w["seed"], traj)
+        assert abs(out.dH - want["dH"]) < 1e-10 * max(1.0, abs(want["H0"]))
+        assert abs(out.H0 - want["H0"]) < 1e-10 * abs(want["H0"])
+        assert abs(out.u - want["u"]) == 0.0
+        assert bool(out.accept) == want["accept"]
+        assert out.cg_solves == want["cg_solves"] == w["n_md"] + 1
+        assert abs(out.cg_iterations - want["cg_iters"]) <= 2 * out.cg_solves
+        assert out.max_true_residual < 1e-11
+        assert rel(phi.cpu().numpy(), want["phi"]) < 1e-10
+        phi_np = want["phi"]
+
+
+def test_trajectory_deterministic_and_rejection_restores():
+    w = synth.WORKLOADS["l3_nt8"]
+    c = hmc.Context(hmc.Params(L=3, Nt=8, U=2.0, beta=2.0, n_md=2, traj_length=3.0,
+                               cg_tol=1e-12))
+    phi0 = t64(synth.gaussian_field(3, 8, 18, 0.5, scale=0.5))
+    a, b = phi0.clone(), phi0.clone()
+    outs = [c.trajectory(a, 9, t, allow_not_converged=True) for t in range(4)]
+    outs2 = [c.trajectory(b, 9, t, allow_not_converged=True) for t in range(4)]
+    assert torch.equal(a, b)
+    assert [o.dH for o in outs] == [o.dH for o in outs2]
+    # a rejected trajectory leaves phi unchanged
+    for t in range(30):
+        before = a.clone()
+        o = c.trajectory(a, 10, t, allow_not_converged=True)
+        if not o.accept:
+            assert torch.equal(a, before)
+            break

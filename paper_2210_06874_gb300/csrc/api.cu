@@ -262,7 +262,8 @@ int hmc_cg_solve(hmc_ctx* c, const double* phi, const void* chi, void* x, double
     cudaStream_t s = (cudaStream_t)stream;
     std::memset(stats, 0, sizeof(*stats));
     if (cudaMemsetAsync(c->view.status, 0, sizeof(int), s) != cudaSuccess ||
-        cudaMemsetAsync(c->view.bar, 0, 2 * sizeof(unsigned), s) != cudaSuccess)
+        cudaMemsetAsync(c->view.bar, 0, 2 * sizeof(unsigned), s) != cudaSuccess ||
+        cudaMemsetAsync(c->view.scalars, 0, sizeof(double) * kNumScalars, s) != cudaSuccess)
         return HMC_ERR_CUDA;
     int st;
     if (prec == HMC_PREC_FP64)
@@ -303,7 +304,8 @@ int hmc_trajectory(hmc_ctx* c, double* phi, uint64_t seed, uint64_t traj_index, 
     cudaStream_t s = (cudaStream_t)stream;
     std::memset(out, 0, sizeof(*out));
     if (cudaMemsetAsync(c->view.status, 0, sizeof(int), s) != cudaSuccess ||
-        cudaMemsetAsync(c->view.bar, 0, 2 * sizeof(unsigned), s) != cudaSuccess)
+        cudaMemsetAsync(c->view.bar, 0, 2 * sizeof(unsigned), s) != cudaSuccess ||
+        cudaMemsetAsync(c->view.scalars, 0, sizeof(double) * kNumScalars, s) != cudaSuccess)
         return HMC_ERR_CUDA;
     TrajArgs a;
     a.phi = phi;

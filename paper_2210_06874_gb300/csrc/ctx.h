@@ -25,6 +25,7 @@ struct ChainView {
     double *pi, *phi_old;       // double [Nt][V]
     // FP32 workspaces for the mixed path, float2 [Nt][V] each
     float2 *cis_f, *r_f, *p_f, *q_f, *x_f;
+    double* norm_partials;      // per-CTA partial |v|^2 of standalone applies
     // team synchronisation
     unsigned* bar;              // 2 words
     int* status;                // device status word
@@ -34,8 +35,13 @@ struct ChainView {
 
 }  // namespace hmc
 
+namespace hmc {
+struct TcCtx;
+}
+
 struct hmc_ctx {
     hmc_params params;
+    hmc::TcCtx* tc;             // tensor-core path state (tc_kernels.cu)
     int device;
     int num_sms;
     hmc::ChainView view;

@@ -161,7 +161,7 @@ struct CgResult {
 // Conjugate gradient on M M^dag from x = 0 (FP64), CG vectors in the chain
 // workspace (r, p, q).  cis must hold exp(i phi).  Ends with the FP64 true
 // residual, which leaves chi - M M^dag x in r.
-__device__ bool cg_solve(const ChainView& c, Team& tm, const double2* chi, double2* x,
+__device__ inline bool cg_solve(const ChainView& c, Team& tm, const double2* chi, double2* x,
                          double tol, int max_iter, CgResult& res, Smem& sm) {
     double2 *r = c.r, *p = c.p, *q = c.q;
     double v1[1] = {0.0};

@@ -1,17 +1,593 @@
-// tc_kernels.cu -- mixed-precision path (placeholder until the tensor-core
-// contraction lands).
+// tc_kernels.cu -- the mixed-precision path: tensor-core applications of
+// M / M^dag (FP16 split, FP32 accumulate), FP32 conjugate gradient with FP64
+// reliable updates, and the HMC trajectory built on it.  FP64 stays for the
+// true residual, chi = M rho, the force, the Hamiltonian sums and Metropolis.
+#include <cuda_fp16.h>
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <vector>
+
+#include "fp64_path.cuh"
 #include "tc_path.h"
+#include "tc_tile.cuh"
 
 namespace hmc {
 
-int tc_ctx_init(hmc_ctx*) { return HMC_OK; }
-void tc_ctx_free(hmc_ctx*) {}
-int tc_apply(hmc_ctx*, const double*, const float2*, float2*, bool, cudaStream_t) {
-    return HMC_ERR_UNSUPPORTED;
+struct TcCtx {
+    CUtensorMap map_hi, map_lo;
+    int ns_apply;        // slices per tile of standalone applications
+    int n_norm;          // CTAs of the norm pre-pass
+};
+
+namespace tc {
+
+// ---------------------------------------------------------------- epilogues
+template <bool DAG>
+struct EpiStore {
+    const float2* in;
+    float2* out;
+    const float2* cis;
+    int V, Nt;
+    double acc;
+    __device__ __forceinline__ void operator()(int i, int t, float2 w) {
+        const size_t o = (size_t)t * V + i;
+        float sg;
+        if (DAG) {
+            sg = (t == Nt - 1) ? -1.f : 1.f;
+            w = cmulcf(cis[o], w);
+        } else {
+            sg = (t == 0) ? -1.f : 1.f;
+        }
+        const float2 s = in[o];
+        const float2 r = make_float2(s.x - sg * w.x, s.y - sg * w.y);
+        out[o] = r;
+        acc += (double)r.x * r.x + (double)r.y * r.y;
+    }
+};
+
+// M q -> Ap; x_f += alpha p; r_f -= alpha Ap; accumulates |r_f|^2.
+struct EpiCgUpdate {
+    const float2* q;
+    const float2* p;
+    float2* x;
+    float2* r;
+    float alpha;
+    int V;
+    double acc;
+    __device__ __forceinline__ void operator()(int i, int t, float2 w) {
+        const size_t o = (size_t)t * V + i;
+        const float sg = (t == 0) ? -1.f : 1.f;
+        const float2 qv = q[o];
+        const float2 ap = make_float2(qv.x - sg * w.x, qv.y - sg * w.y);
+        const float2 pv = p[o];
+        float2 xv = x[o], rv = r[o];
+        xv.x = fmaf(alpha, pv.x, xv.x);
+        xv.y = fmaf(alpha, pv.y, xv.y);
+        rv.x = fmaf(-alpha, ap.x, rv.x);
+        rv.y = fmaf(-alpha, ap.y, rv.y);
+        x[o] = xv;
+        r[o] = rv;
+        acc += (double)rv.x * rv.x + (double)rv.y * rv.y;
+    }
+};
+
+__device__ __forceinline__ void tile_coords(int tile, int nti, int ns_tile, int Nt, int& i0,
+                                            int& t0, int& ns) {
+    i0 = (tile % nti) * TM;
+    t0 = (tile / nti) * ns_tile;
+    ns = min(ns_tile, Nt - t0);
 }
-int tc_cg(hmc_ctx*, const double*, const double2*, double2*, double, int, cudaStream_t) {
-    return HMC_ERR_UNSUPPORTED;
+
+// All tensor-core tiles of one application, spread over the team.
+template <bool DAG, class Epi>
+__device__ bool apply_team(const ChainView& c, const Team& tm, TcState& st,
+                           const CUtensorMap* mhi, const CUtensorMap* mlo, int ns_tile,
+                           const float2* in, float scale, float inv, Epi& epi) {
+    const int nti = c.Vr / TM, ntt = (c.Nt + ns_tile - 1) / ns_tile;
+    for (int tile = tm.rank; tile < nti * ntt; tile += tm.size) {
+        int i0, t0, ns;
+        tile_coords(tile, nti, ns_tile, c.Nt, i0, t0, ns);
+        if (!tc_tile<DAG>(st, mhi, mlo, c.V, c.Nt, c.Vp, i0, t0, ns, in, c.cis_f, scale, inv,
+                          epi))
+            return false;
+    }
+    return true;
 }
-int tc_trajectory(hmc_ctx*, const TrajArgs&, cudaStream_t) { return HMC_ERR_UNSUPPORTED; }
+
+// ---------------------------------------------------------------- standalone
+// cis_f = exp(i phi) in FP32 and per-CTA partial |in|^2.
+__global__ void k_prep(const double* __restrict__ phi, float2* __restrict__ cis_f,
+                       const float2* __restrict__ in, double* __restrict__ partials, int N) {
+    double acc[1] = {0.0};
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < N; e += gridDim.x * blockDim.x) {
+        float s, co;
+        sincosf((float)phi[e], &s, &co);
+        cis_f[e] = make_float2(co, s);
+        const float2 v = in[e];
+        acc[0] += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    block_reduce<1>(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc[0];
+}
+
+template <bool DAG>
+__global__ void __launch_bounds__(NTHR, 1)
+    k_apply(const __grid_constant__ CUtensorMap mhi, const __grid_constant__ CUtensorMap mlo,
+            ChainView c, int ns_tile, const float2* in, float2* out, int n_norm) {
+    extern __shared__ __align__(1024) uint8_t dyn[];
+    TcState st;
+    tc_setup(st, dyn, c.status);
+    __shared__ double s_n2;
+    if (threadIdx.x == 0) {
+        double n2 = 0.0;
+        for (int j = 0; j < n_norm; ++j) n2 += c.norm_partials[j];
+        s_n2 = n2;
+    }
+    __syncthreads();
+    float scale, inv;
+    vector_scale(s_n2, scale, inv);
+    EpiStore<DAG> epi{in, out, c.cis_f, c.V, c.Nt, 0.0};
+    const int nti = c.Vr / TM;
+    int i0, t0, ns;
+    tile_coords(blockIdx.x, nti, ns_tile, c.Nt, i0, t0, ns);
+    tc_tile<DAG>(st, &mhi, &mlo, c.V, c.Nt, c.Vp, i0, t0, ns, in, c.cis_f, scale, inv, epi);
+    tc_teardown(st);
+}
+
+// ---------------------------------------------------------------- mixed CG
+struct MixedResult {
+    int iterations;
+    int reliable_updates;
+    double true_res;
+    int status;
+};
+
+struct PersistentArgs {
+    int ns_tile;
+    double tol;
+    int max_iter;
+    double ru_delta;
+};
+
+// FP64 true residual of x64: r64 = chi - M (M^dag x64); returns |r64|^2.
+__device__ bool f64_residual(const ChainView& c, Team& tm, f64::Smem& sm, const double2* chi,
+                             double2* x64, double& rr) {
+    f64::EpiArgs ea = {};
+    f64::apply_team<true, f64::EPI_STORE>(c, tm, x64, c.q, ea, sm);
+    if (!team_barrier(tm)) return false;
+    ea.chi = chi;
+    ea.r = c.r;
+    double v[1] = {f64::apply_team<false, f64::EPI_RESIDUAL>(c, tm, c.q, nullptr, ea, sm)};
+    if (!team_sum<1>(tm, v)) return false;
+    rr = v[0];
+    return true;
+}
+
+// FP32 CG on the tensor-core operator with FP64 reliable updates
+// (Sleijpen-van der Vorst style, as used in lattice QCD solvers): whenever
+// the iterated residual has dropped by ru_delta since the last update, or
+// claims convergence, the FP32 increment is folded into the FP64 solution,
+// the true residual chi - M M^dag x is recomputed in FP64 and replaces the
+// iterated one; the search direction is kept.  Stops on the FP64 true
+// residual.  Needs c.cis (FP64) and c.cis_f (FP32) of the current phi.
+__device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& sm64,
+                         const CUtensorMap* mhi, const CUtensorMap* mlo,
+                         const PersistentArgs& pa, const double2* chi, double2* x64,
+                         MixedResult& res) {
+    float2 *rf = c.r_f, *pf = c.p_f, *qf = c.q_f, *xf = c.x_f;
+    double v2[2] = {0.0, 0.0};
+    HMC_TEAM_ELEMS(e, c, tm) {
+        const double2 ch = chi[e];
+        x64[e] = make_double2(0.0, 0.0);
+        const float2 rv = make_float2((float)ch.x, (float)ch.y);
+        rf[e] = rv;
+        pf[e] = rv;
+        xf[e] = make_float2(0.f, 0.f);
+        v2[0] += ch.x * ch.x + ch.y * ch.y;
+        v2[1] += (double)rv.x * rv.x + (double)rv.y * rv.y;
+    }
+    if (!team_sum<2>(tm, v2)) return false;
+    const double chi2 = v2[0];
+    double rr = v2[1], pp = rr, rmax = rr, rr_true = chi2;
+    res.iterations = 0;
+    res.reliable_updates = 0;
+    res.status = HMC_OK;
+    res.true_res = 0.0;
+    if (!(chi2 > 0.0)) {
+        if (!finite_d(chi2)) res.status = HMC_ERR_NONFINITE;
+        return true;
+    }
+    const double stop = pa.tol * pa.tol * chi2;
+    const double ru2 = pa.ru_delta * pa.ru_delta;
+    int it = 0;
+    bool conv = false;
+    while (it < pa.max_iter) {
+        float sc, inv;
+        vector_scale(pp, sc, inv);
+        EpiStore<true> eq{pf, qf, c.cis_f, c.V, c.Nt, 0.0};
+        if (!apply_team<true>(c, tm, st, mhi, mlo, pa.ns_tile, pf, sc, inv, eq)) return false;
+        double vq[1] = {eq.acc};
+        if (!team_sum<1>(tm, vq)) return false;
+        const double qq = vq[0];
+        if (!finite_d(qq) || !(qq > 0.0)) { res.status = HMC_ERR_NONFINITE; break; }
+        const double alpha = rr / qq;
+        vector_scale(qq, sc, inv);
+        EpiCgUpdate eu{qf, pf, xf, rf, (float)alpha, c.V, 0.0};
+        if (!apply_team<false>(c, tm, st, mhi, mlo, pa.ns_tile, qf, sc, inv, eu)) return false;
+        double vr[1] = {eu.acc};
+        if (!team_sum<1>(tm, vr)) return false;
+        double rr_new = vr[0];
+        ++it;
+        if (!finite_d(rr_new)) { res.status = HMC_ERR_NONFINITE; break; }
+        bool refresh = false;
+        if (rr_new <= stop || rr_new <= ru2 * rmax) {
+            HMC_TEAM_ELEMS(e, c, tm) {
+                const float2 d = xf[e];
+                double2 xv = x64[e];
+                xv.x += (double)d.x;
+                xv.y += (double)d.y;
+                x64[e] = xv;
+                xf[e] = make_float2(0.f, 0.f);
+            }
+            if (!team_barrier(tm)) return false;
+            if (!f64_residual(c, tm, sm64, chi, x64, rr_true)) return false;
+            ++res.reliable_updates;
+            if (!finite_d(rr_true)) { res.status = HMC_ERR_NONFINITE; break; }
+            if (rr_true <= stop) { conv = true; break; }
+            rr_new = rr_true;
+            rmax = rr_true;
+            refresh = true;
+        }
+        const double beta = rr_new / rr;
+        rr = rr_new;
+        const float bf = (float)beta;
+        HMC_TEAM_ELEMS(e, c, tm) {
+            float2 rv;
+            if (refresh) {
+                const double2 r64 = c.r[e];
+                rv = make_float2((float)r64.x, (float)r64.y);
+                rf[e] = rv;
+            } else {
+                rv = rf[e];
+            }
+            const float2 pv = pf[e];
+            pf[e] = make_float2(fmaf(bf, pv.x, rv.x), fmaf(bf, pv.y, rv.y));
+        }
+        pp = rr + beta * beta * pp;
+        if (!team_barrier(tm)) return false;
+    }
+    res.iterations = it;
+    if (!conv && res.status == HMC_OK) {
+        // iteration cap: fold in the last increment and report the true residual
+        HMC_TEAM_ELEMS(e, c, tm) {
+            const float2 d = xf[e];
+            double2 xv = x64[e];
+            xv.x += (double)d.x;
+            xv.y += (double)d.y;
+            x64[e] = xv;
+        }
+        if (!team_barrier(tm)) return false;
+        if (!f64_residual(c, tm, sm64, chi, x64, rr_true)) return false;
+        res.status = HMC_ERR_CG_NOT_CONVERGED;
+    }
+    res.true_res = sqrt(rr_true / chi2);
+    if (!finite_d(res.true_res)) res.status = HMC_ERR_NONFINITE;
+    return true;
+}
+
+__device__ __forceinline__ Team make_team(const ChainView& c) {
+    Team tm;
+    tm.rank = blockIdx.x;
+    tm.size = gridDim.x;
+    tm.bar = c.bar;
+    tm.status = c.status;
+    tm.partials = c.partials;
+    tm.slot = 0;
+    return tm;
+}
+
+__device__ __forceinline__ void set_phases(const ChainView& c, const Team& tm,
+                                           const double* phi) {
+    HMC_TEAM_ELEMS(e, c, tm) {
+        double s, co;
+        sincos(phi[e], &s, &co);
+        c.cis[e] = make_double2(co, s);
+        c.cis_f[e] = make_float2((float)co, (float)s);
+    }
+}
+
+// scalars: [0] iterations [1] true residual [2] status [3] reliable updates
+__global__ void __launch_bounds__(NTHR, 1)
+    k_cg(const __grid_constant__ CUtensorMap mhi, const __grid_constant__ CUtensorMap mlo,
+         ChainView c, PersistentArgs pa, const double* phi, const double2* chi, double2* x) {
+    extern __shared__ __align__(1024) uint8_t dyn[];
+    __shared__ f64::Smem sm64;
+    TcState st;
+    tc_setup(st, dyn, c.status);
+    Team tm = make_team(c);
+    set_phases(c, tm, phi);
+    MixedResult res{};
+    bool ok = team_barrier(tm);
+    if (ok) ok = cg_mixed(c, tm, st, sm64, &mhi, &mlo, pa, chi, x, res);
+    if (ok && tm.rank == 0 && threadIdx.x == 0) {
+        c.scalars[0] = res.iterations;
+        c.scalars[1] = res.true_res;
+        c.scalars[2] = res.status;
+        c.scalars[3] = res.reliable_updates;
+    }
+    tc_teardown(st);
+}
+
+// One HMC trajectory with the mixed solver (same steps as the FP64 one).
+__global__ void __launch_bounds__(NTHR, 1)
+    k_trajectory(const __grid_constant__ CUtensorMap mhi,
+                 const __grid_constant__ CUtensorMap mlo, ChainView c, PersistentArgs pa,
+                 TrajArgs a) {
+    extern __shared__ __align__(1024) uint8_t dyn[];
+    __shared__ f64::Smem sm64;
+    TcState st;
+    tc_setup(st, dyn, c.status);
+    Team tm = make_team(c);
+    double* phi = a.phi;
+    const double inv_dU = 1.0 / (c.delta * c.U);
+    const double rsqrt2 = 0.70710678118654752440;
+    double h0[3] = {0.0, 0.0, 0.0};
+    HMC_TEAM_ELEMS(e, c, tm) {
+        const double2 zp = normal_pair(philox_draw(a.seed, kStreamMomentum, a.traj, a.chain, e));
+        const double2 zr = normal_pair(philox_draw(a.seed, kStreamNoise, a.traj, a.chain, e));
+        const double ph = phi[e];
+        c.pi[e] = zp.x;
+        const double2 rho = make_double2(zr.x * rsqrt2, zr.y * rsqrt2);
+        c.rho[e] = rho;
+        c.phi_old[e] = ph;
+        double s, co;
+        sincos(ph, &s, &co);
+        c.cis[e] = make_double2(co, s);
+        c.cis_f[e] = make_float2((float)co, (float)s);
+        h0[0] += ph * ph;
+        h0[1] += rho.x * rho.x + rho.y * rho.y;
+        h0[2] += zp.x * zp.x;
+    }
+    bool ok = team_sum<3>(tm, h0);
+    const double H0 = 0.5 * h0[0] * inv_dU + h0[1] + 0.5 * h0[2];
+    f64::EpiArgs ea = {};
+    if (ok) {
+        f64::apply_team<false, f64::EPI_STORE>(c, tm, c.rho, c.chi, ea, sm64);
+        ok = team_barrier(tm);
+    }
+    int iters = 0, solves = 0, rus = 0, status = HMC_OK;
+    double max_res = 0.0;
+    ea.phi = phi;
+    ea.pi = c.pi;
+    ea.inv_dU = inv_dU;
+    const double ed = a.eps * c.delta;
+    for (int step = 0; ok && step <= a.n_md; ++step) {
+        if (step > 0) {
+            HMC_TEAM_ELEMS(e, c, tm) {
+                const double ph = fma(ed, c.pi[e], phi[e]);
+                phi[e] = ph;
+                double s, co;
+                sincos(ph, &s, &co);
+                c.cis[e] = make_double2(co, s);
+                c.cis_f[e] = make_float2((float)co, (float)s);
+            }
+            if (!(ok = team_barrier(tm))) break;
+        }
+        MixedResult res{};
+        if (!(ok = cg_mixed(c, tm, st, sm64, &mhi, &mlo, pa, c.chi, c.x, res))) break;
+        iters += res.iterations;
+        rus += res.reliable_updates;
+        ++solves;
+        max_res = fmax(max_res, res.true_res);
+        if (res.status != HMC_OK && status == HMC_OK) status = res.status;
+        ea.kick = ((step == 0 || step == a.n_md) ? 0.5 : 1.0) * ed;
+        f64::apply_team<true, f64::EPI_FORCE>(c, tm, c.x, nullptr, ea, sm64);
+        ok = team_barrier(tm);
+    }
+    double h1[3] = {0.0, 0.0, 0.0};
+    if (ok) {
+        HMC_TEAM_ELEMS(e, c, tm) {
+            const double ph = phi[e], pv = c.pi[e];
+            const double2 ch = c.chi[e], xv = c.x[e];
+            h1[0] += ph * ph;
+            h1[1] += ch.x * xv.x + ch.y * xv.y;
+            h1[2] += pv * pv;
+        }
+        ok = team_sum<3>(tm, h1);
+    }
+    if (ok) {
+        const double H1 = 0.5 * h1[0] * inv_dU + h1[1] + 0.5 * h1[2];
+        const double dH = H1 - H0;
+        const double u =
+            uniform_pair(philox_draw(a.seed, kStreamMetropolis, a.traj, a.chain, 0)).x;
+        const bool accept = u < exp(-dH);
+        if (!accept) {
+            HMC_TEAM_ELEMS(e, c, tm) phi[e] = c.phi_old[e];
+        }
+        if (tm.rank == 0 && threadIdx.x == 0) {
+            c.scalars[kTrajDH] = dH;
+            c.scalars[kTrajH0] = H0;
+            c.scalars[kTrajH1] = H1;
+            c.scalars[kTrajU] = u;
+            c.scalars[kTrajAccept] = accept ? 1.0 : 0.0;
+            c.scalars[kTrajIters] = iters;
+            c.scalars[kTrajSolves] = solves;
+            c.scalars[kTrajRU] = rus;
+            c.scalars[kTrajMaxRes] = max_res;
+            c.scalars[kTrajStatus] = status;
+        }
+    }
+    tc_teardown(st);
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------- host side
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+static bool make_map(CUtensorMap* m, void* base, int Vr, int Vp) {
+    auto enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)Vp, (cuuint64_t)Vr};
+    cuuint64_t strides[1] = {(cuuint64_t)Vp * 2};
+    cuuint32_t box[2] = {(cuuint32_t)tc::KCH, (cuuint32_t)tc::TM};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+// Smallest slices-per-tile in {8, 16, 32, 64} with at most `slots` tiles.
+static int pick_ns(int nti, int Nt, int slots) {
+    int ns = 8;
+    while (ns < tc::NMAX / 2 && nti * ((Nt + ns - 1) / ns) > slots) ns *= 2;
+    return ns;
+}
+
+static void* dev_alloc(hmc_ctx* c, size_t bytes, bool* ok) {
+    if (!*ok) return nullptr;
+    void* p = nullptr;
+    if (c->n_allocs >= (int)(sizeof(c->allocs) / sizeof(c->allocs[0])) ||
+        cudaMalloc(&p, bytes) != cudaSuccess) {
+        *ok = false;
+        return nullptr;
+    }
+    c->allocs[c->n_allocs++] = p;
+    cudaMemset(p, 0, bytes);
+    return p;
+}
+
+int tc_ctx_init(hmc_ctx* c) {
+    ChainView& v = c->view;
+    const int V = v.V;
+    v.Vr = ((V + tc::TM - 1) / tc::TM) * tc::TM;
+    v.Vp = ((V + tc::KCH - 1) / tc::KCH) * tc::KCH;
+    std::vector<double> E((size_t)V * V);
+    if (cudaMemcpy(E.data(), v.E, E.size() * sizeof(double), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+        return HMC_ERR_CUDA;
+    // E = E_hi + 2^-11 E_lo with both parts in fp16, padded with zeros
+    std::vector<__half> hi((size_t)v.Vr * v.Vp), lo((size_t)v.Vr * v.Vp);
+    for (int r = 0; r < v.Vr; ++r)
+        for (int k = 0; k < v.Vp; ++k) {
+            const double e = (r < V && k < V) ? E[(size_t)r * V + k] : 0.0;
+            const __half h = __float2half_rn((float)e);
+            const double rem = (e - (double)__half2float(h)) * 2048.0;
+            hi[(size_t)r * v.Vp + k] = h;
+            lo[(size_t)r * v.Vp + k] = __float2half_rn((float)rem);
+        }
+    bool ok = true;
+    const size_t N = (size_t)v.N;
+    void* dhi = dev_alloc(c, hi.size() * sizeof(__half), &ok);
+    void* dlo = dev_alloc(c, lo.size() * sizeof(__half), &ok);
+    v.cis_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
+    v.r_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
+    v.p_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
+    v.q_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
+    v.x_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
+    v.norm_partials = (double*)dev_alloc(c, 1024 * sizeof(double), &ok);
+    if (!ok) return HMC_ERR_CUDA;
+    if (cudaMemcpy(dhi, hi.data(), hi.size() * sizeof(__half), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(dlo, lo.data(), lo.size() * sizeof(__half), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+        return HMC_ERR_CUDA;
+    v.E_hi = dhi;
+    v.E_lo = dlo;
+    c->tc = new TcCtx();
+    if (!make_map(&c->tc->map_hi, dhi, v.Vr, v.Vp) || !make_map(&c->tc->map_lo, dlo, v.Vr, v.Vp))
+        return HMC_ERR_CUDA;
+    c->tc->ns_apply = pick_ns(v.Vr / tc::TM, v.Nt, c->num_sms);
+    c->tc->n_norm = std::min(1024, std::max(1, (int)((N + 1023) / 1024)));
+    const void* kernels[] = {(const void*)tc::k_apply<false>, (const void*)tc::k_apply<true>,
+                             (const void*)tc::k_cg, (const void*)tc::k_trajectory};
+    for (const void* k : kernels)
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tc::kSmemBytes) != cudaSuccess)
+            return HMC_ERR_CUDA;
+    return HMC_OK;
+}
+
+void tc_ctx_free(hmc_ctx* c) {
+    delete c->tc;
+    c->tc = nullptr;
+}
+
+int tc_apply(hmc_ctx* c, const double* phi, const float2* in, float2* out, bool dag,
+             cudaStream_t s) {
+    const ChainView& v = c->view;
+    tc::k_prep<<<c->tc->n_norm, 256, 0, s>>>(phi, v.cis_f, in, v.norm_partials, v.N);
+    const int ns = c->tc->ns_apply;
+    const int tiles = (v.Vr / tc::TM) * ((v.Nt + ns - 1) / ns);
+    if (dag)
+        tc::k_apply<true><<<tiles, tc::NTHR, tc::kSmemBytes, s>>>(
+            c->tc->map_hi, c->tc->map_lo, v, ns, in, out, c->tc->n_norm);
+    else
+        tc::k_apply<false><<<tiles, tc::NTHR, tc::kSmemBytes, s>>>(
+            c->tc->map_hi, c->tc->map_lo, v, ns, in, out, c->tc->n_norm);
+    return cudaGetLastError() == cudaSuccess ? HMC_OK : HMC_ERR_CUDA;
+}
+
+static int team_size(hmc_ctx* c, const void* kernel) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, tc::NTHR, tc::kSmemBytes) !=
+            cudaSuccess ||
+        occ < 1)
+        return -1;
+    const ChainView& v = c->view;
+    const int f64_tiles = ((v.V + f64::TI - 1) / f64::TI) * ((v.Nt + f64::TT - 1) / f64::TT);
+    const int tc_tiles = (v.Vr / tc::TM) * ((v.Nt + 7) / 8);
+    int want = std::max(f64_tiles, tc_tiles);
+    int g = std::min(c->num_sms * occ, kMaxTeam);
+    return std::max(1, std::min(g, want));
+}
+
+static tc::PersistentArgs persistent_args(hmc_ctx* c, int grid, double tol, int max_iter) {
+    tc::PersistentArgs pa;
+    pa.ns_tile = pick_ns(c->view.Vr / tc::TM, c->view.Nt, grid);
+    pa.tol = tol;
+    pa.max_iter = max_iter;
+    pa.ru_delta = c->params.ru_delta;
+    return pa;
+}
+
+int tc_cg(hmc_ctx* c, const double* phi, const double2* chi, double2* x, double tol,
+          int max_iter, cudaStream_t s) {
+    const int grid = team_size(c, (const void*)tc::k_cg);
+    if (grid < 1) return HMC_ERR_CUDA;
+    tc::PersistentArgs pa = persistent_args(c, grid, tol, max_iter);
+    ChainView v = c->view;
+    void* args[] = {&c->tc->map_hi, &c->tc->map_lo, &v, &pa, &phi, &chi, &x};
+    return cudaLaunchCooperativeKernel((const void*)tc::k_cg, dim3(grid), dim3(tc::NTHR), args,
+                                       tc::kSmemBytes, s) == cudaSuccess
+               ? HMC_OK
+               : HMC_ERR_CUDA;
+}
+
+int tc_trajectory(hmc_ctx* c, const TrajArgs& a, cudaStream_t s) {
+    const int grid = team_size(c, (const void*)tc::k_trajectory);
+    if (grid < 1) return HMC_ERR_CUDA;
+    tc::PersistentArgs pa = persistent_args(c, grid, a.tol, a.max_iter);
+    ChainView v = c->view;
+    TrajArgs av = a;
+    void* args[] = {&c->tc->map_hi, &c->tc->map_lo, &v, &pa, &av};
+    return cudaLaunchCooperativeKernel((const void*)tc::k_trajectory, dim3(grid),
+                                       dim3(tc::NTHR), args, tc::kSmemBytes, s) == cudaSuccess
+               ? HMC_OK
+               : HMC_ERR_CUDA;
+}
 
 }  // namespace hmc

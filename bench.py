@@ -38,6 +38,10 @@ def parse():
     ap.add_argument("--workload", default="l6_nt32")
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "mixed"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="trajectory", choices=["trajectory", "apply"],
+                    help="trajectory: HMC trajectories/s; apply: M-applications/s")
+    ap.add_argument("--applies", type=int, default=20,
+                    help="apply mode: applications of M per step")
     ap.add_argument("--therm", type=int, default=None,
                     help="untimed thermalisation trajectories before warm-up")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -338,8 +342,93 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def apply_bytes(V, Nt, prec):
+    """Algorithmic HBM bytes of one application: E once (FP64, or its FP16
+    hi/lo split), the input and output vectors, the phase field phi and the
+    phase table exp(i phi) written and read once."""
+    N = V * Nt
+    if prec == "fp64":
+        return 8.0 * V * V + 16.0 * N * 2 + 8.0 * N + 16.0 * N * 2
+    return 4.0 * V * V + 8.0 * N * 2 + 8.0 * N + 8.0 * N * 2
+
+
+def run_apply(args):
+    """M-applications/s of hmc_apply_M on the workload's lattice."""
+    import torch
+    from paper_2210_06874_gb300 import build_lib, hmc, synth
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    build_lib.build()
+    name = args.workload
+    w, params, prec = workload_params(name, args.precision)
+    ctx = hmc.Context(params)
+    V, Nt = params.V, params.Nt
+    dev = torch.device("cuda", local_rank)
+    phi = torch.from_numpy(synth.gaussian_field(w["seed"], Nt, V, w["beta"] / Nt * w["U"],
+                                                scale=0.5)).to(dev)
+    dt = torch.complex128 if prec == "fp64" else torch.complex64
+    p = hmc.PREC_FP64 if prec == "fp64" else hmc.PREC_MIXED
+    psi = torch.from_numpy(synth.complex_gaussian(w["seed"] + 1, Nt, V)).to(dev).to(dt)
+    out = torch.empty_like(psi)
+    for _ in range(args.warmup):
+        ctx.apply_M(phi, psi, out, prec=p)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    clocks = ClockSampler(local_rank)
+    torch.cuda.synchronize()
+    clocks.start()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        for _ in range(args.applies):
+            ctx.apply_M(phi, psi, out, prec=p)
+        e.record(stream)
+        e.synchronize()
+        total_ms += s.elapsed_time(e)
+    clk = clocks.stop()
+    n = args.steps * args.applies
+    per_ms = total_ms / n
+    flop = flops_per_apply(V, Nt)
+    byts = apply_bytes(V, Nt, prec)
+    peaks, kind = load_peaks()
+    if prec == "fp64":
+        peak = measure_dgemm_tflops(torch)
+        roof = {"bound": "alu", "achieved": flop / (per_ms * 1e-3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "peak_source": "measured cuBLAS DGEMM 4096^3"}
+    else:
+        peak = peaks.get("bf16_tflops", FALLBACK["bf16_tflops"])
+        roof = {"bound": "tensor", "achieved": flop / (per_ms * 1e-3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s",
+                "peak_source": "%s bf16 dense burst (fp16 has the same rate)" % kind}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["hbm"] = {"achieved_gbs": byts / (per_ms * 1e-3) / 1e9,
+                   "peak_gbs": peaks.get("hbm_gbs", FALLBACK["hbm_gbs"]),
+                   "algorithmic_bytes": byts}
+    roof["hbm"]["frac"] = roof["hbm"]["achieved_gbs"] / roof["hbm"]["peak_gbs"]
+    line = {"metric": METRIC, "value": 1e3 / per_ms, "unit": "M-applications/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == "fp64" else "f16-split/f32",
+            "data": "synthetic",
+            "config": {"workload": name, "mode": "apply", "precision": prec, "V": V, "Nt": Nt,
+                       "applies_per_step": args.applies,
+                       "l2": "flushed (256 MB write) between timed steps"},
+            "gpu_launches": n * 2 if prec != "fp64" else n * 2,
+            "roofline": roof, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.mode == "apply" and args.impl == "ours":
+        run_apply(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -161,6 +161,33 @@ int hmc_trajectory(hmc_ctx* ctx, double* phi, uint64_t seed, uint64_t traj_index
 int hmc_rng_draw(uint64_t seed, uint32_t stream_id, uint64_t traj, uint32_t chain,
                  int64_t n, uint32_t* raw, double* z0, double* z1, void* stream);
 
+/* FP64 CG solve of (M M^dag) x = chi that allocates no device memory.
+ *
+ * The paper has no counterpart; this is a library convenience.  Callers that
+ * may not call cudaMalloc -- code running under CUDA graph capture, hosts
+ * whose device memory comes from a framework pool or a fixed real-time
+ * budget, plugins barred from growing the device heap -- cannot create an
+ * hmc_ctx.  This call needs none: it runs the same FP64 CG as hmc_cg_solve
+ * with HMC_PREC_FP64 (same algorithm, stopping rule and stats), with its
+ * scratch in one static device array of about 2.1 MB that every GPU which
+ * loads the library holds until the process exits.
+ *
+ *   E      device, double [V][V], the transfer matrix exp(delta*kappa*h),
+ *          row-major and exactly symmetric (e.g. from hmc_get_transfer_matrix)
+ *   L, Nt  lattice: V = 2 L^2 sites, Nt slices; V * Nt must not exceed
+ *          32768, larger sizes return HMC_ERR_UNSUPPORTED before any launch
+ *   phi    device, double [Nt][V]; chi, x device complex128 [Nt][V]
+ *   stats  host; the call synchronises `stream`
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call on a device shares the one array:
+ * calls that overlap on the GPU (other streams, other host threads) race
+ * and give wrong results; serialise them.  The barrier, status and output
+ * words are cleared on every call.  Errors as hmc_cg_solve. */
+int hmc_cg_solve_noalloc(const double* E, int L, int Nt, const double* phi, const void* chi,
+                         void* x, double tol, int max_iter, hmc_cg_stats* stats, void* stream);
+
 /* Library version string (static storage). */
 const char* hmc_version(void);
 

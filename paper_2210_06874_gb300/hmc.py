@@ -80,6 +80,9 @@ SIGNATURES = {
     "hmc_rng_draw": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
                                     ctypes.c_uint32, ctypes.c_int64, _P, _P, _P, _P]),
     "hmc_version": (ctypes.c_char_p, []),
+    "hmc_cg_solve_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P,
+                                            ctypes.c_double, ctypes.c_int,
+                                            ctypes.POINTER(hmc_cg_stats), _P]),
 }
 
 
@@ -247,6 +250,18 @@ def rng_draw(seed, stream_id, traj, chain, n, device=None):
     _check("hmc_rng_draw", lib.hmc_rng_draw(seed, stream_id, traj, chain, n, _ptr(raw),
                                             _ptr(z0), _ptr(z1), _stream()))
     return raw, z0, z1
+
+
+def cg_solve_noalloc(E, L, Nt, phi, chi, x, tol, max_iter):
+    """hmc_cg_solve_noalloc: FP64 CG with the library's static scratch (no
+    device allocation inside the call).  E: float64 [V, V], phi: float64
+    [Nt, V], chi and x: complex128 [Nt, V], all contiguous on the current
+    device; x is written.  Returns (code, hmc_cg_stats)."""
+    lib = load_library()
+    st = hmc_cg_stats()
+    code = lib.hmc_cg_solve_noalloc(_ptr(E), L, Nt, _ptr(phi), _ptr(chi), _ptr(x), tol,
+                                    max_iter, ctypes.byref(st), _stream())
+    return code, st
 
 
 def version():

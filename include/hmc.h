@@ -79,7 +79,12 @@ typedef struct hmc_params {
     int cg_max_iter;     /* CG iteration cap per solve */
     int precision;       /* hmc_precision used by hmc_trajectory */
     double ru_delta;     /* mixed CG: reliable update when |r| < ru_delta * max|r|
-                            since the last update (0 selects 0.05) */
+                            since the last update (0 selects the default) */
+    int team_ctas;       /* CTAs of a persistent launch (0: automatic) */
+    int tile_slices;     /* time slices per tensor-core tile, one of 8, 16, 32
+                            (0: automatic) */
+    int inner_ctas;      /* CTAs running the FP32 iterations of the mixed CG
+                            (0: automatic; the FP64 steps use all CTAs) */
 } hmc_params;
 
 typedef struct hmc_cg_stats {

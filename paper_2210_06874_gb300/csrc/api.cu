@@ -138,6 +138,11 @@ static int valid_params(const hmc_params* p) {
     if (!(p->cg_tol > 0.0) || p->cg_max_iter < 1) return 0;
     if (p->precision != HMC_PREC_FP64 && p->precision != HMC_PREC_MIXED) return 0;
     if (p->ru_delta < 0.0 || p->ru_delta >= 1.0) return 0;
+    if (p->team_ctas < 0 || p->team_ctas > 1024) return 0;
+    if (p->inner_ctas < 0 || p->inner_ctas > 1024) return 0;
+    if (p->tile_slices != 0 && p->tile_slices != 8 && p->tile_slices != 16 &&
+        p->tile_slices != 32)
+        return 0;
     // indices of [Nt][V] vectors are 32-bit in the kernels
     const long long N = 2LL * p->L * p->L * (long long)p->Nt;
     if (N > (1LL << 30)) return 0;
@@ -192,9 +197,9 @@ int hmc_ctx_create(const hmc_params* p, hmc_ctx** out) {
     v.rho = (double2*)ctx_alloc(c, N * sizeof(double2), &ok);
     v.pi = (double*)ctx_alloc(c, N * sizeof(double), &ok);
     v.phi_old = (double*)ctx_alloc(c, N * sizeof(double), &ok);
-    v.bar = (unsigned*)ctx_alloc(c, 2 * sizeof(unsigned), &ok);
+    v.bar = (unsigned*)ctx_alloc(c, 8 * sizeof(unsigned), &ok);
     v.status = (int*)ctx_alloc(c, sizeof(int), &ok);
-    v.partials = (double*)ctx_alloc(c, sizeof(double) * kSlots * kMaxTeam * kVals, &ok);
+    v.partials = (double*)ctx_alloc(c, sizeof(double) * kPartialDoubles, &ok);
     v.scalars = (double*)ctx_alloc(c, sizeof(double) * kNumScalars, &ok);
     if (ok && cudaMemcpy(dE, E.data(), E.size() * sizeof(double), cudaMemcpyHostToDevice) !=
                   cudaSuccess)
@@ -262,7 +267,7 @@ int hmc_cg_solve(hmc_ctx* c, const double* phi, const void* chi, void* x, double
     cudaStream_t s = (cudaStream_t)stream;
     std::memset(stats, 0, sizeof(*stats));
     if (cudaMemsetAsync(c->view.status, 0, sizeof(int), s) != cudaSuccess ||
-        cudaMemsetAsync(c->view.bar, 0, 2 * sizeof(unsigned), s) != cudaSuccess ||
+        cudaMemsetAsync(c->view.bar, 0, 8 * sizeof(unsigned), s) != cudaSuccess ||
         cudaMemsetAsync(c->view.scalars, 0, sizeof(double) * kNumScalars, s) != cudaSuccess)
         return HMC_ERR_CUDA;
     int st;
@@ -304,7 +309,7 @@ int hmc_trajectory(hmc_ctx* c, double* phi, uint64_t seed, uint64_t traj_index, 
     cudaStream_t s = (cudaStream_t)stream;
     std::memset(out, 0, sizeof(*out));
     if (cudaMemsetAsync(c->view.status, 0, sizeof(int), s) != cudaSuccess ||
-        cudaMemsetAsync(c->view.bar, 0, 2 * sizeof(unsigned), s) != cudaSuccess ||
+        cudaMemsetAsync(c->view.bar, 0, 8 * sizeof(unsigned), s) != cudaSuccess ||
         cudaMemsetAsync(c->view.scalars, 0, sizeof(double) * kNumScalars, s) != cudaSuccess)
         return HMC_ERR_CUDA;
     TrajArgs a;

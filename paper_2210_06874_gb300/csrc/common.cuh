@@ -82,18 +82,20 @@ constexpr uint64_t kWaitLimitNs = 20ull * 1000ull * 1000ull * 1000ull;  // 20 s
 // ---------------------------------------------------------------- team
 // A team is a set of co-resident CTAs of one persistent (cooperative)
 // launch that work on one Markov chain.  bar[0] = arrival count,
-// bar[1] = generation.  partials: [kSlots][kMaxTeam][kVals] doubles.
+// bar[1] = generation.  partials: per-CTA partial sums [kMaxTeam][kVals],
+// followed by the published team totals [kVals].
 constexpr int kMaxTeam = 1024;
-constexpr int kSlots = 4;
 constexpr int kVals = 4;
+constexpr int kSlots = 1;          // partial-sum buffers (one suffices, see team_sum)
+constexpr size_t kPartialDoubles = (size_t)kMaxTeam * kVals + kVals;
 
 struct Team {
     int rank;          // CTA rank within the team
     int size;          // number of CTAs in the team
     unsigned* bar;     // 2 words, zero-initialised
     int* status;       // shared device status word (hmc_status, 0 = ok)
-    double* partials;  // kSlots * kMaxTeam * kVals
-    int slot;          // rotating partials slot (identical on all CTAs)
+    double* partials;  // kPartialDoubles
+    int slot;          // unused (kept for layout stability)
 };
 
 __device__ __forceinline__ bool team_failed(const Team& tm) {
@@ -104,42 +106,10 @@ __device__ __forceinline__ void set_status(int* status, int code) {
     atomicCAS(status, 0, code);
 }
 
-// Bounded generation barrier over the team.  Returns false (on every
-// thread of the CTA) if the team's status is set or the wait timed out.
-__device__ inline bool team_barrier(Team& tm) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        if (tm.size > 1) {
-            cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(tm.bar[0]);
-            cuda::atomic_ref<unsigned, cuda::thread_scope_device> gen(tm.bar[1]);
-            __threadfence();
-            const unsigned g = gen.load(cuda::memory_order_acquire);
-            if (cnt.fetch_add(1u, cuda::memory_order_acq_rel) == (unsigned)(tm.size - 1)) {
-                cnt.store(0u, cuda::memory_order_relaxed);
-                gen.store(g + 1u, cuda::memory_order_release);
-            } else {
-                const uint64_t t0 = global_ns();
-                unsigned ns = 32;
-                while (gen.load(cuda::memory_order_acquire) == g) {
-                    __nanosleep(ns);
-                    if (ns < 256) ns <<= 1;
-                    if (team_failed(tm)) { ok = 0; break; }
-                    if (global_ns() - t0 > kWaitLimitNs) {
-                        set_status(tm.status, HMC_ERR_TIMEOUT);
-                        ok = 0;
-                        break;
-                    }
-                }
-            }
-            __threadfence();
-        }
-        if (team_failed(tm)) ok = 0;
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
 // Fixed-order CTA reduction of NV doubles; result valid on thread 0.
@@ -167,36 +137,103 @@ __device__ __forceinline__ void block_reduce(double (&v)[NV]) {
     }
 }
 
-// Deterministic team-wide sum of NV values: every CTA of the team gets the
-// same bits (each sums the per-CTA partials in the same fixed order).
-// Contains a team barrier; returns false if the team failed.
+// Team barrier fused with a deterministic sum of NV values (NV = 0: plain
+// barrier).  Every CTA writes its partials, then arrives on the counter; the
+// last CTA to arrive sums the partials of all ranks in rank order (a fixed
+// order, so every run and every CTA gets the same bits), publishes the
+// totals and flips the generation word; the others spin (bounded) on the
+// generation and read the totals.  One buffer suffices: a CTA can write its
+// next partials only after passing this barrier, and the last arriver has
+// read every partial before it releases the barrier.
+// Returns false on every thread of the CTA if the team failed or a wait
+// timed out.
 template <int NV>
-__device__ inline bool team_sum(Team& tm, double (&v)[NV]) {
-    static_assert(NV <= kVals, "too many values");
-    __shared__ double s_out[NV];
-    block_reduce<NV>(v);
-    double* part = tm.partials + (size_t)tm.slot * kMaxTeam * kVals;
-    if (threadIdx.x == 0)
+__device__ inline bool team_sync(Team& tm, double* v) {
+    __shared__ int s_ok;
+    __shared__ int s_last;
+    __shared__ double s_out[NV > 0 ? NV : 1];
+    if constexpr (NV > 0) block_reduce<NV>(*reinterpret_cast<double(*)[NV]>(v));
+    if (tm.size == 1) {
+        if (threadIdx.x == 0) {
 #pragma unroll
-        for (int j = 0; j < NV; ++j) part[tm.rank * kVals + j] = v[j];
-    tm.slot = (tm.slot + 1) % kSlots;
-    if (!team_barrier(tm)) return false;
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-#pragma unroll
-        for (int j = 0; j < NV; ++j) {
-            double a = 0.0;
-            for (int r = lane; r < tm.size; r += 32) a += ((volatile double*)part)[r * kVals + j];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-            if (lane == 0) s_out[j] = a;
+            for (int j = 0; j < NV; ++j) s_out[j] = v[j];
+            s_ok = !team_failed(tm);
         }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] = s_out[j];
+        const int ok = s_ok;
+        __syncthreads();
+        return ok != 0;
+    }
+    double* totals = tm.partials + (size_t)kMaxTeam * kVals;
+    cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(tm.bar[0]);
+    cuda::atomic_ref<unsigned, cuda::thread_scope_device> gen(tm.bar[1]);
+    unsigned g = 0;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) tm.partials[tm.rank * kVals + j] = v[j];
+        g = gen.load(cuda::memory_order_relaxed);
+        __threadfence();
+        s_last = cnt.fetch_add(1u, cuda::memory_order_acq_rel) == (unsigned)(tm.size - 1);
+    }
+    __syncthreads();
+    if (s_last) {
+        // last arriver: fixed-order sum of all partials by warp 0, publish
+        if (NV > 0 && threadIdx.x < 32) {
+            __threadfence();
+            const int lane = threadIdx.x;
+#pragma unroll
+            for (int j = 0; j < NV; ++j) {
+                double a = 0.0;
+                for (int r = lane; r < tm.size; r += 32)
+                    a += ((volatile double*)tm.partials)[r * kVals + j];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+                if (lane == 0) {
+                    totals[j] = a;
+                    s_out[j] = a;
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            cnt.store(0u, cuda::memory_order_relaxed);
+            __threadfence();
+            gen.store(g + 1u, cuda::memory_order_release);
+            s_ok = !team_failed(tm);
+        }
+    } else if (threadIdx.x == 0) {
+        int ok = 1;
+        const uint64_t t0 = global_ns();
+        for (unsigned n = 1; ld_acquire_u32(&tm.bar[1]) == g; ++n) {
+            if ((n & 1023u) == 0) {
+                if (team_failed(tm)) { ok = 0; break; }
+                if (global_ns() - t0 > kWaitLimitNs) {
+                    set_status(tm.status, HMC_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+#pragma unroll
+        for (int j = 0; j < NV; ++j) s_out[j] = ((volatile double*)totals)[j];
+        s_ok = ok && !team_failed(tm);
     }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < NV; ++j) v[j] = s_out[j];
+    const int ok = s_ok;
     __syncthreads();
-    return true;
+    return ok != 0;
+}
+
+__device__ inline bool team_barrier(Team& tm) { return team_sync<0>(tm, nullptr); }
+
+template <int NV>
+__device__ inline bool team_sum(Team& tm, double (&v)[NV]) {
+    return team_sync<NV>(tm, v);
 }
 
 __device__ __forceinline__ bool finite_d(double a) { return isfinite(a); }

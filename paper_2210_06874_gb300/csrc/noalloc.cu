@@ -24,7 +24,7 @@ namespace {
 // Largest space-time volume N = V * Nt the static scratch holds.
 constexpr int kNoAllocMaxN = 32768;
 constexpr size_t kVecBytes = sizeof(double2) * (size_t)kNoAllocMaxN;
-constexpr size_t kPartialBytes = sizeof(double) * kSlots * kMaxTeam * kVals;
+constexpr size_t kPartialBytes = sizeof(double) * kPartialDoubles;
 // layout: cis | r | p | q | partials | scalars[16] | bar[2] | status
 constexpr size_t kOffR = kVecBytes;
 constexpr size_t kOffP = 2 * kVecBytes;

@@ -23,26 +23,36 @@ struct TcCtx {
 namespace tc {
 
 // ---------------------------------------------------------------- epilogues
+// Each epilogue splits into load (global reads of what output (t, i) needs)
+// and store (arithmetic and writes), so the tile can batch the reads.
 template <bool DAG>
 struct EpiStore {
     const float2* in;
     float2* out;
     const float2* cis;
     int V, Nt;
-    double acc;
-    __device__ __forceinline__ void operator()(int i, int t, float2 w) {
+    float acc;   // per-thread partial |out|^2 (at most 32 terms; FP32 suffices)
+    struct In {
+        float2 s, ph;
+    };
+    __device__ __forceinline__ In load(int i, int t) const {
         const size_t o = (size_t)t * V + i;
+        In v;
+        v.s = in[o];
+        v.ph = DAG ? cis[o] : make_float2(1.f, 0.f);
+        return v;
+    }
+    __device__ __forceinline__ void store(int i, int t, const In& v, float2 w) {
         float sg;
         if (DAG) {
             sg = (t == Nt - 1) ? -1.f : 1.f;
-            w = cmulcf(cis[o], w);
+            w = cmulcf(v.ph, w);
         } else {
             sg = (t == 0) ? -1.f : 1.f;
         }
-        const float2 s = in[o];
-        const float2 r = make_float2(s.x - sg * w.x, s.y - sg * w.y);
-        out[o] = r;
-        acc += (double)r.x * r.x + (double)r.y * r.y;
+        const float2 r = make_float2(v.s.x - sg * w.x, v.s.y - sg * w.y);
+        out[(size_t)t * V + i] = r;
+        acc = fmaf(r.x, r.x, fmaf(r.y, r.y, acc));
     }
 };
 
@@ -54,21 +64,72 @@ struct EpiCgUpdate {
     float2* r;
     float alpha;
     int V;
-    double acc;
-    __device__ __forceinline__ void operator()(int i, int t, float2 w) {
+    float acc;   // per-thread partial |r|^2
+    struct In {
+        float2 q, p, x, r;
+    };
+    __device__ __forceinline__ In load(int i, int t) const {
+        const size_t o = (size_t)t * V + i;
+        In v;
+        v.q = q[o];
+        v.p = p[o];
+        v.x = x[o];
+        v.r = r[o];
+        return v;
+    }
+    __device__ __forceinline__ void store(int i, int t, const In& v, float2 w) {
         const size_t o = (size_t)t * V + i;
         const float sg = (t == 0) ? -1.f : 1.f;
-        const float2 qv = q[o];
-        const float2 ap = make_float2(qv.x - sg * w.x, qv.y - sg * w.y);
-        const float2 pv = p[o];
-        float2 xv = x[o], rv = r[o];
-        xv.x = fmaf(alpha, pv.x, xv.x);
-        xv.y = fmaf(alpha, pv.y, xv.y);
+        const float2 ap = make_float2(v.q.x - sg * w.x, v.q.y - sg * w.y);
+        float2 xv = v.x, rv = v.r;
+        xv.x = fmaf(alpha, v.p.x, xv.x);
+        xv.y = fmaf(alpha, v.p.y, xv.y);
         rv.x = fmaf(-alpha, ap.x, rv.x);
         rv.y = fmaf(-alpha, ap.y, rv.y);
         x[o] = xv;
         r[o] = rv;
-        acc += (double)rv.x * rv.x + (double)rv.y * rv.y;
+        acc = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, acc));
+    }
+};
+
+// CG direction step fused into M^dag: at the tile's own (t, i) form
+// p_new = r + beta p_old (r from the FP64 residual after a reliable update,
+// which is then also stored as the new FP32 r), store p_new, and
+// q = M^dag p_new = p_new - s_{t+1} e^{-i phi_t} w; accumulates |q|^2.
+struct EpiDirection {
+    SrcDirection d;
+    float2* p_new;
+    float2* r_out;     // written when d.refresh
+    float2* q;
+    const float2* cis;
+    int Nt;
+    float acc;   // per-thread partial |q|^2
+    struct In {
+        float2 r, p, ph;
+    };
+    __device__ __forceinline__ In load(int i, int t) const {
+        const size_t o = (size_t)t * d.V + i;
+        In v;
+        if (d.refresh) {
+            const double2 r64 = d.r64[o];
+            v.r = make_float2((float)r64.x, (float)r64.y);
+        } else {
+            v.r = d.r[o];
+        }
+        v.p = d.p_old[o];
+        v.ph = cis[o];
+        return v;
+    }
+    __device__ __forceinline__ void store(int i, int t, const In& v, float2 w) {
+        const size_t o = (size_t)t * d.V + i;
+        const float2 pv = make_float2(fmaf(d.beta, v.p.x, v.r.x), fmaf(d.beta, v.p.y, v.r.y));
+        if (d.refresh) r_out[o] = v.r;
+        p_new[o] = pv;
+        const float sg = (t == Nt - 1) ? -1.f : 1.f;
+        w = cmulcf(v.ph, w);
+        const float2 qv = make_float2(pv.x - sg * w.x, pv.y - sg * w.y);
+        q[o] = qv;
+        acc = fmaf(qv.x, qv.x, fmaf(qv.y, qv.y, acc));
     }
 };
 
@@ -80,16 +141,15 @@ __device__ __forceinline__ void tile_coords(int tile, int nti, int ns_tile, int 
 }
 
 // All tensor-core tiles of one application, spread over the team.
-template <bool DAG, class Epi>
+template <bool DAG, class Src, class Epi>
 __device__ bool apply_team(const ChainView& c, const Team& tm, TcState& st,
                            const CUtensorMap* mhi, const CUtensorMap* mlo, int ns_tile,
-                           const float2* in, float scale, float inv, Epi& epi) {
+                           const Src& src, float scale, float inv, Epi& epi) {
     const int nti = c.Vr / TM, ntt = (c.Nt + ns_tile - 1) / ns_tile;
     for (int tile = tm.rank; tile < nti * ntt; tile += tm.size) {
         int i0, t0, ns;
         tile_coords(tile, nti, ns_tile, c.Nt, i0, t0, ns);
-        if (!tc_tile<DAG>(st, mhi, mlo, c.V, c.Nt, c.Vp, i0, t0, ns, in, c.cis_f, scale, inv,
-                          epi))
+        if (!tc_tile<DAG>(st, mhi, mlo, c.V, c.Nt, c.Vp, i0, t0, ns, src, scale, inv, epi))
             return false;
     }
     return true;
@@ -127,11 +187,17 @@ __global__ void __launch_bounds__(NTHR, 1)
     __syncthreads();
     float scale, inv;
     vector_scale(s_n2, scale, inv);
-    EpiStore<DAG> epi{in, out, c.cis_f, c.V, c.Nt, 0.0};
+    EpiStore<DAG> epi{in, out, c.cis_f, c.V, c.Nt, 0.f};
     const int nti = c.Vr / TM;
     int i0, t0, ns;
     tile_coords(blockIdx.x, nti, ns_tile, c.Nt, i0, t0, ns);
-    tc_tile<DAG>(st, &mhi, &mlo, c.V, c.Nt, c.Vp, i0, t0, ns, in, c.cis_f, scale, inv, epi);
+    if (DAG) {
+        SrcPlain src{in, c.V};
+        tc_tile<DAG>(st, &mhi, &mlo, c.V, c.Nt, c.Vp, i0, t0, ns, src, scale, inv, epi);
+    } else {
+        SrcPhase src{in, c.cis_f, c.V};
+        tc_tile<DAG>(st, &mhi, &mlo, c.V, c.Nt, c.Vp, i0, t0, ns, src, scale, inv, epi);
+    }
     tc_teardown(st);
 }
 
@@ -145,6 +211,7 @@ struct MixedResult {
 
 struct PersistentArgs {
     int ns_tile;
+    int inner;         // CTAs of the FP32 inner loop
     double tol;
     int max_iter;
     double ru_delta;
@@ -170,26 +237,43 @@ __device__ bool f64_residual(const ChainView& c, Team& tm, f64::Smem& sm, const 
 // claims convergence, the FP32 increment is folded into the FP64 solution,
 // the true residual chi - M M^dag x is recomputed in FP64 and replaces the
 // iterated one; the search direction is kept.  Stops on the FP64 true
-// residual.  Needs c.cis (FP64) and c.cis_f (FP32) of the current phi.
+// residual.
+//
+// Two teams: the FP32 iterations run on the first `inner` CTAs (one CTA
+// for small lattices, so an iteration needs no inter-CTA barrier), the FP64
+// steps on all CTAs of the launch (FP64 is ~1/1700 of the tensor rate, so it
+// is spread over as many SMs as possible).  The other CTAs wait at the
+// outer barrier while the inner loop runs.  Two inner synchronisations per
+// iteration: the direction update p = r + beta p happens inside the M^dag
+// application (operand build and epilogue, into a second p buffer), the
+// x / r update inside the M one.  Needs c.cis and c.cis_f of the current phi.
+enum SegmentEnd : int { kSegUpdate = 1, kSegMaxIter = 2, kSegNonfinite = 3 };
+
 __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& sm64,
                          const CUtensorMap* mhi, const CUtensorMap* mlo,
                          const PersistentArgs& pa, const double2* chi, double2* x64,
                          MixedResult& res) {
-    float2 *rf = c.r_f, *pf = c.p_f, *qf = c.q_f, *xf = c.x_f;
+    float2 *rf = c.r_f, *pf = c.p_f, *pn = c.p2_f, *qf = c.q_f, *xf = c.x_f;
+    const int inner_size = min(max(pa.inner, 1), tm.size);
+    const bool in_inner = tm.rank < inner_size;
+    Team ti = tm;
+    ti.size = inner_size;
+    ti.bar = c.bar + 2;
     double v2[2] = {0.0, 0.0};
     HMC_TEAM_ELEMS(e, c, tm) {
         const double2 ch = chi[e];
         x64[e] = make_double2(0.0, 0.0);
         const float2 rv = make_float2((float)ch.x, (float)ch.y);
         rf[e] = rv;
-        pf[e] = rv;
+        pf[e] = make_float2(0.f, 0.f);
         xf[e] = make_float2(0.f, 0.f);
         v2[0] += ch.x * ch.x + ch.y * ch.y;
         v2[1] += (double)rv.x * rv.x + (double)rv.y * rv.y;
     }
     if (!team_sum<2>(tm, v2)) return false;
     const double chi2 = v2[0];
-    double rr = v2[1], pp = rr, rmax = rr, rr_true = chi2;
+    double rr = v2[1], pp = rr, rmax = rr, rr_true = chi2, beta = 0.0;
+    bool refresh = false;
     res.iterations = 0;
     res.reliable_updates = 0;
     res.status = HMC_OK;
@@ -202,75 +286,76 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
     const double ru2 = pa.ru_delta * pa.ru_delta;
     int it = 0;
     bool conv = false;
-    while (it < pa.max_iter) {
-        float sc, inv;
-        vector_scale(pp, sc, inv);
-        EpiStore<true> eq{pf, qf, c.cis_f, c.V, c.Nt, 0.0};
-        if (!apply_team<true>(c, tm, st, mhi, mlo, pa.ns_tile, pf, sc, inv, eq)) return false;
-        double vq[1] = {eq.acc};
-        if (!team_sum<1>(tm, vq)) return false;
-        const double qq = vq[0];
-        if (!finite_d(qq) || !(qq > 0.0)) { res.status = HMC_ERR_NONFINITE; break; }
-        const double alpha = rr / qq;
-        vector_scale(qq, sc, inv);
-        EpiCgUpdate eu{qf, pf, xf, rf, (float)alpha, c.V, 0.0};
-        if (!apply_team<false>(c, tm, st, mhi, mlo, pa.ns_tile, qf, sc, inv, eu)) return false;
-        double vr[1] = {eu.acc};
-        if (!team_sum<1>(tm, vr)) return false;
-        double rr_new = vr[0];
-        ++it;
-        if (!finite_d(rr_new)) { res.status = HMC_ERR_NONFINITE; break; }
-        bool refresh = false;
-        if (rr_new <= stop || rr_new <= ru2 * rmax) {
-            HMC_TEAM_ELEMS(e, c, tm) {
-                const float2 d = xf[e];
-                double2 xv = x64[e];
-                xv.x += (double)d.x;
-                xv.y += (double)d.y;
-                x64[e] = xv;
-                xf[e] = make_float2(0.f, 0.f);
+    volatile double* seg = c.scalars + 12;   // [0] end reason, [1] iterations
+    for (;;) {
+        if (in_inner) {
+            int reason = kSegMaxIter;
+            while (it < pa.max_iter) {
+                // p_new = r + beta p; q = M^dag p_new
+                float sc, inv;
+                vector_scale(pp, sc, inv);
+                SrcDirection dir{rf, c.r, pf, (float)beta, refresh, c.V};
+                EpiDirection ed{dir, pn, rf, qf, c.cis_f, c.Nt, 0.f};
+                if (!apply_team<true>(c, ti, st, mhi, mlo, pa.ns_tile, dir, sc, inv, ed))
+                    return false;
+                double vq[1] = {(double)ed.acc};
+                if (!team_sum<1>(ti, vq)) return false;
+                float2* t = pf;
+                pf = pn;
+                pn = t;
+                refresh = false;
+                const double qq = vq[0];
+                if (!finite_d(qq) || !(qq > 0.0)) { reason = kSegNonfinite; break; }
+                const double alpha = rr / qq;
+                // Ap = M q; x += alpha p; r -= alpha Ap
+                vector_scale(qq, sc, inv);
+                SrcPhase srcq{qf, c.cis_f, c.V};
+                EpiCgUpdate eu{qf, pf, xf, rf, (float)alpha, c.V, 0.f};
+                if (!apply_team<false>(c, ti, st, mhi, mlo, pa.ns_tile, srcq, sc, inv, eu))
+                    return false;
+                double vr[1] = {(double)eu.acc};
+                if (!team_sum<1>(ti, vr)) return false;
+                const double rr_new = vr[0];
+                ++it;
+                if (!finite_d(rr_new)) { reason = kSegNonfinite; break; }
+                if (rr_new <= stop || rr_new <= ru2 * rmax) { reason = kSegUpdate; break; }
+                beta = rr_new / rr;
+                rr = rr_new;
+                pp = rr + beta * beta * pp;
             }
-            if (!team_barrier(tm)) return false;
-            if (!f64_residual(c, tm, sm64, chi, x64, rr_true)) return false;
-            ++res.reliable_updates;
-            if (!finite_d(rr_true)) { res.status = HMC_ERR_NONFINITE; break; }
-            if (rr_true <= stop) { conv = true; break; }
-            rr_new = rr_true;
-            rmax = rr_true;
-            refresh = true;
-        }
-        const double beta = rr_new / rr;
-        rr = rr_new;
-        const float bf = (float)beta;
-        HMC_TEAM_ELEMS(e, c, tm) {
-            float2 rv;
-            if (refresh) {
-                const double2 r64 = c.r[e];
-                rv = make_float2((float)r64.x, (float)r64.y);
-                rf[e] = rv;
-            } else {
-                rv = rf[e];
+            if (tm.rank == 0 && threadIdx.x == 0) {
+                seg[0] = reason;
+                seg[1] = it;
             }
-            const float2 pv = pf[e];
-            pf[e] = make_float2(fmaf(bf, pv.x, rv.x), fmaf(bf, pv.y, rv.y));
         }
-        pp = rr + beta * beta * pp;
         if (!team_barrier(tm)) return false;
-    }
-    res.iterations = it;
-    if (!conv && res.status == HMC_OK) {
-        // iteration cap: fold in the last increment and report the true residual
+        const int reason = (int)seg[0];
+        it = (int)seg[1];
+        if (reason == kSegNonfinite) { res.status = HMC_ERR_NONFINITE; break; }
+        // fold the FP32 increment into x64; FP64 true residual on all CTAs
         HMC_TEAM_ELEMS(e, c, tm) {
             const float2 d = xf[e];
             double2 xv = x64[e];
             xv.x += (double)d.x;
             xv.y += (double)d.y;
             x64[e] = xv;
+            xf[e] = make_float2(0.f, 0.f);
         }
         if (!team_barrier(tm)) return false;
         if (!f64_residual(c, tm, sm64, chi, x64, rr_true)) return false;
-        res.status = HMC_ERR_CG_NOT_CONVERGED;
+        ++res.reliable_updates;
+        if (!finite_d(rr_true)) { res.status = HMC_ERR_NONFINITE; break; }
+        if (rr_true <= stop) { conv = true; break; }
+        if (reason == kSegMaxIter) break;
+        // continue from the true residual; keep the direction
+        beta = rr_true / rr;
+        rr = rr_true;
+        rmax = rr_true;
+        pp = rr + beta * beta * pp;
+        refresh = true;
     }
+    res.iterations = it;
+    if (!conv && res.status == HMC_OK) res.status = HMC_ERR_CG_NOT_CONVERGED;
     res.true_res = sqrt(rr_true / chi2);
     if (!finite_d(res.true_res)) res.status = HMC_ERR_NONFINITE;
     return true;
@@ -496,6 +581,7 @@ int tc_ctx_init(hmc_ctx* c) {
     v.cis_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
     v.r_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
     v.p_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
+    v.p2_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
     v.q_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
     v.x_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
     v.norm_partials = (double*)dev_alloc(c, 1024 * sizeof(double), &ok);
@@ -551,13 +637,20 @@ static int team_size(hmc_ctx* c, const void* kernel) {
     const int f64_tiles = ((v.V + f64::TI - 1) / f64::TI) * ((v.Nt + f64::TT - 1) / f64::TT);
     const int tc_tiles = (v.Vr / tc::TM) * ((v.Nt + 7) / 8);
     int want = std::max(f64_tiles, tc_tiles);
+    if (c->params.team_ctas > 0) want = c->params.team_ctas;
     int g = std::min(c->num_sms * occ, kMaxTeam);
     return std::max(1, std::min(g, want));
 }
 
 static tc::PersistentArgs persistent_args(hmc_ctx* c, int grid, double tol, int max_iter) {
     tc::PersistentArgs pa;
-    pa.ns_tile = pick_ns(c->view.Vr / tc::TM, c->view.Nt, grid);
+    const ChainView& v = c->view;
+    // inner team: one CTA while the whole lattice fits in a handful of tiles
+    // (a single CTA needs no inter-CTA barrier), else the whole launch
+    pa.inner = (v.Vr / tc::TM) * ((v.Nt + 31) / 32) <= 2 ? 1 : grid;
+    if (c->params.inner_ctas > 0) pa.inner = std::min(c->params.inner_ctas, grid);
+    pa.ns_tile = pick_ns(v.Vr / tc::TM, v.Nt, pa.inner);
+    if (c->params.tile_slices > 0) pa.ns_tile = c->params.tile_slices;
     pa.tol = tol;
     pa.max_iter = max_iter;
     pa.ru_delta = c->params.ru_delta;

@@ -9,14 +9,13 @@
 //                                          so that |v| s is in [2^12, 2^13))
 //     E v s ~= E_hi B_hi + 2^-11 (E_hi B_lo + E_lo B_hi)
 // accumulated in two TMEM accumulators (main at column 0, correction at
-// column 128).  The dropped E_lo B_lo term is 2^-22 relative.
+// column 64).  The dropped E_lo B_lo term is 2^-22 relative.
 //
-// B is built by the CTA's threads straight into the 128-byte-swizzled
-// K-major layout the MMA reads: for M the phase exp(i phi_{t-1}) is
-// multiplied in; for M^dag the source slice is t+1 and the conjugate phase
-// of the target slice is applied in the epilogue.  Two pipeline stages: while
-// the MMAs of chunk k run, the TMA of E and the B build of chunk k+1 fill the
-// other stage.
+// B is built by six warps straight into the 128-byte-swizzled K-major
+// layout the MMA reads: for M the phase exp(i phi_{t-1}) is multiplied in;
+// for M^dag the source slice is t+1 and the conjugate phase of the target
+// slice is applied in the epilogue.  A ring of kStages operand stages with
+// full/empty mbarriers keeps TMA, B production and MMA issue overlapped.
 #pragma once
 
 #include "tc_ptx.cuh"
@@ -26,24 +25,31 @@ namespace tc {
 
 constexpr int TM = 128;         // sites per tile (MMA M)
 constexpr int KCH = 64;         // K per chunk: one 128-byte swizzle row of fp16
-constexpr int NMAX = 128;       // max MMA N (= 2 * slices per tile)
-constexpr int NTHR = 256;       // threads per CTA
-constexpr int kStages = 2;
-constexpr uint32_t kTmemCols = 256;    // main accumulator at 0, correction at 128
-constexpr uint32_t kCorrCol = 128;
+constexpr int NMAX = 64;        // max MMA N (= 2 * slices per tile)
+constexpr int NTHR = 256;       // threads per CTA (8 warps)
+constexpr int kStages = 4;      // depth of the operand ring
+constexpr uint32_t kTmemCols = 128;    // main accumulator at 0, correction at 64
+constexpr uint32_t kCorrCol = 64;
 constexpr float kLoScale = 2048.f;     // 2^11
 constexpr float kLoInv = 1.f / 2048.f;
 constexpr uint32_t kATileBytes = TM * 128;
+// warp roles
+constexpr int kWarpTma = 0;            // lane 0 issues the TMA loads of E
+constexpr int kWarpMma = 1;            // lane 0 issues tcgen05.mma
+constexpr int kFirstBWarp = 2;         // warps 2..7 build the B operand
+constexpr int kNumBWarps = 6;
+constexpr int kFirstEpiWarp = 4;       // warps 4..7 read TMEM (lane quarter = warp % 4)
+static_assert((NMAX / 2) * 8 <= 2 * kNumBWarps * 32, "build_B covers at most 2 items/thread");
 
 struct TileSmem {
     uint8_t a_hi[kStages][TM * 128];
     uint8_t a_lo[kStages][TM * 128];
     uint8_t b_hi[kStages][NMAX * 128];
     uint8_t b_lo[kStages][NMAX * 128];
-    uint64_t tma_bar[kStages];
-    uint64_t mma_bar[kStages];
+    uint64_t full[kStages];    // TMA bytes + one arrival per B warp
+    uint64_t empty[kStages];   // MMA commit: the stage may be refilled
+    uint64_t acc_full;         // MMA commit after a tile's last chunk
     uint32_t tmem_base;
-    int ok;
 };
 constexpr size_t kSmemBytes = sizeof(TileSmem) + 1024;  // + alignment slack
 
@@ -74,58 +80,126 @@ __device__ __forceinline__ int source_slice(int t, int Nt) {
     return DAG ? (t + 1 == Nt ? 0 : t + 1) : (t == 0 ? Nt - 1 : t - 1);
 }
 
+// Sources of the B operand: value of the vector the tile contracts with E,
+// at source slice ts and sites kb..kb+7 (kb a multiple of 8, kb + 8 <= V)
+// or at one site k.
+struct SrcPlain {                       // u = in
+    const float2* in;
+    int V;
+    __device__ __forceinline__ void load8(int ts, int kb, float2 (&v)[8]) const {
+        const float4* s4 = reinterpret_cast<const float4*>(in + (size_t)ts * V + kb);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float4 a = s4[e];
+            v[2 * e] = make_float2(a.x, a.y);
+            v[2 * e + 1] = make_float2(a.z, a.w);
+        }
+    }
+    __device__ __forceinline__ float2 load1(int ts, int k) const { return in[(size_t)ts * V + k]; }
+};
+
+struct SrcPhase {                       // u = exp(i phi) * in
+    const float2* in;
+    const float2* cis;
+    int V;
+    __device__ __forceinline__ void load8(int ts, int kb, float2 (&v)[8]) const {
+        const float4* s4 = reinterpret_cast<const float4*>(in + (size_t)ts * V + kb);
+        const float4* p4 = reinterpret_cast<const float4*>(cis + (size_t)ts * V + kb);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float4 a = s4[e], c = p4[e];
+            v[2 * e] = cmulf(make_float2(c.x, c.y), make_float2(a.x, a.y));
+            v[2 * e + 1] = cmulf(make_float2(c.z, c.w), make_float2(a.z, a.w));
+        }
+    }
+    __device__ __forceinline__ float2 load1(int ts, int k) const {
+        const size_t o = (size_t)ts * V + k;
+        return cmulf(cis[o], in[o]);
+    }
+};
+
+// u = p_new = r + beta p_old, the CG direction update done on the fly; r is
+// the FP32 iterate, or (refresh) the FP64 true residual rounded to FP32.
+struct SrcDirection {
+    const float2* r;
+    const double2* r64;
+    const float2* p_old;
+    float beta;
+    bool refresh;
+    int V;
+    __device__ __forceinline__ float2 one(size_t o) const {
+        float2 rv;
+        if (refresh) {
+            const double2 d = r64[o];
+            rv = make_float2((float)d.x, (float)d.y);
+        } else {
+            rv = r[o];
+        }
+        const float2 pv = p_old[o];
+        return make_float2(fmaf(beta, pv.x, rv.x), fmaf(beta, pv.y, rv.y));
+    }
+    __device__ __forceinline__ void load8(int ts, int kb, float2 (&v)[8]) const {
+        const size_t o = (size_t)ts * V + kb;
+        if (refresh) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = one(o + e);
+            return;
+        }
+        const float4* r4 = reinterpret_cast<const float4*>(r + o);
+        const float4* p4 = reinterpret_cast<const float4*>(p_old + o);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float4 a = r4[e], b = p4[e];
+            v[2 * e] = make_float2(fmaf(beta, b.x, a.x), fmaf(beta, b.y, a.y));
+            v[2 * e + 1] = make_float2(fmaf(beta, b.z, a.z), fmaf(beta, b.w, a.w));
+        }
+    }
+    __device__ __forceinline__ float2 load1(int ts, int k) const {
+        return one((size_t)ts * V + k);
+    }
+};
+
 // Fill the B operand of K chunk [k0, k0+64) for the tile's slices t0..t0+ns-1
 // (rows 2*tt (re) and 2*tt+1 (im); rows up to nrows-1 beyond 2*ns are zero).
-template <bool DAG>
-__device__ __forceinline__ void build_B(const float2* __restrict__ in,
-                                        const float2* __restrict__ cis, int V, int Nt, int t0,
-                                        int ns, int nrows, int k0, float scale, uint8_t* bhi,
-                                        uint8_t* blo) {
+template <bool DAG, class Src>
+__device__ __forceinline__ void build_B(const Src& src, int V, int Nt, int t0, int ns,
+                                        int nrows, int k0, float scale, uint8_t* bhi,
+                                        uint8_t* blo, int ptid, int nprod) {
     const int items = (nrows >> 1) * 8;
-    for (int w = threadIdx.x; w < items; w += NTHR) {
-        const int tt = w >> 3, grp = w & 7;
-        const int kb = k0 + grp * 8;
-        float re[8], im[8];
+    // at most two items per producer thread (nrows <= 64, 192 producers):
+    // issue the global loads of both before converting either
+    float2 v[2][8];
+    int wi[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int w = ptid + j * nprod;
+        wi[j] = w;
+        if (w >= items) continue;
+        const int tt = w >> 3, kb = k0 + (w & 7) * 8;
         if (tt < ns) {
             const int ts = source_slice<DAG>(t0 + tt, Nt);
-            const float2* src = in + (size_t)ts * V + kb;
-            const float2* ph = cis + (size_t)ts * V + kb;
-            float2 v[8];
             if (kb + 8 <= V) {
-                const float4* s4 = reinterpret_cast<const float4*>(src);
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float4 a = s4[e];
-                    v[2 * e] = make_float2(a.x, a.y);
-                    v[2 * e + 1] = make_float2(a.z, a.w);
-                }
-                if (!DAG) {
-                    const float4* p4 = reinterpret_cast<const float4*>(ph);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const float4 a = p4[e];
-                        v[2 * e] = cmulf(make_float2(a.x, a.y), v[2 * e]);
-                        v[2 * e + 1] = cmulf(make_float2(a.z, a.w), v[2 * e + 1]);
-                    }
-                }
+                src.load8(ts, kb, v[j]);
             } else {
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    v[e] = make_float2(0.f, 0.f);
-                    if (kb + e < V) {
-                        v[e] = src[e];
-                        if (!DAG) v[e] = cmulf(ph[e], v[e]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                re[e] = v[e].x * scale;
-                im[e] = v[e].y * scale;
+                for (int e = 0; e < 8; ++e)
+                    v[j][e] = (kb + e < V) ? src.load1(ts, kb + e) : make_float2(0.f, 0.f);
             }
         } else {
 #pragma unroll
-            for (int e = 0; e < 8; ++e) re[e] = im[e] = 0.f;
+            for (int e = 0; e < 8; ++e) v[j][e] = make_float2(0.f, 0.f);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int w = wi[j];
+        if (w >= items) continue;
+        const int tt = w >> 3, grp = w & 7;
+        float re[8], im[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            re[e] = v[j][e].x * scale;
+            im[e] = v[j][e].y * scale;
         }
         uint4 hr, lr, hm, lm;
         split8(re, hr, lr);
@@ -141,7 +215,8 @@ __device__ __forceinline__ void build_B(const float2* __restrict__ in,
 // Per-CTA state of the tensor-core tile pipeline (set up once per launch).
 struct TcState {
     TileSmem* sm;
-    uint32_t gchunk;   // chunks processed so far by this CTA (mbarrier phases)
+    uint32_t gchunk;   // chunks processed so far by this CTA (ring phases)
+    uint32_t ntile;    // tiles processed so far (accumulator phases)
     int* status;
 };
 
@@ -150,12 +225,14 @@ __device__ inline void tc_setup(TcState& st, uint8_t* dyn, int* status) {
     TileSmem& sm = tile_smem(dyn);
     st.sm = &sm;
     st.gchunk = 0;
+    st.ntile = 0;
     st.status = status;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(smem_u32(&sm.tma_bar[s]), 1);
-            mbar_init(smem_u32(&sm.mma_bar[s]), 1);
+            mbar_init(smem_u32(&sm.full[s]), 1 + kNumBWarps);
+            mbar_init(smem_u32(&sm.empty[s]), 1);
         }
+        mbar_init(smem_u32(&sm.acc_full), 1);
         fence_mbar_init();
     }
     if ((threadIdx.x >> 5) == 0) {
@@ -167,13 +244,12 @@ __device__ inline void tc_setup(TcState& st, uint8_t* dyn, int* status) {
     fence_after_sync();
 }
 
-// Tear-down: wait (bounded) for the last MMAs, free TMEM.  All threads call it.
+// Tear-down: wait (bounded) for the last tile's MMAs, free TMEM.  All
+// threads call it.
 __device__ inline void tc_teardown(TcState& st) {
     TileSmem& sm = *st.sm;
-    if (st.gchunk > 0) {
-        const uint32_t g = st.gchunk - 1;
-        mbar_wait(smem_u32(&sm.mma_bar[g & 1]), (g >> 1) & 1, st.status);
-    }
+    if (st.ntile > 0 && *((volatile int*)st.status) != 0)
+        mbar_wait(smem_u32(&sm.acc_full), (st.ntile - 1) & 1, st.status);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -192,44 +268,44 @@ __device__ __forceinline__ void vector_scale(double n2, float& scale, float& inv
 }
 
 // One output tile: target slices t0 .. t0+ns-1 (ns <= NMAX/2), sites
-// i0 .. i0+127.  Epi(i, t, w) receives w = (E u)_{i} for the tile's source
-// slice of target t (unscaled, before shift sign and phase).  Returns false
-// if a bounded wait failed (status set).  All threads call it.
-template <bool DAG, class Epi>
+// i0 .. i0+127.  Warp-specialised: warp 0 streams E_hi/E_lo chunks with TMA,
+// warps 2..7 build the B chunks, warp 1 issues the MMAs as soon as a stage
+// is full and releases it with tcgen05.commit; kStages chunks are in flight.
+// The epilogue runs on warps 4..7: Epi::load(i, t) fetches what the output
+// (t, i) needs, Epi::store(i, t, in, w) receives w = (E u)_i for the tile's
+// source slice of target t (unscaled; before shift sign and phase).
+// Returns false if a bounded wait failed (status set).  All threads call it.
+template <bool DAG, class Src, class Epi>
 __device__ bool tc_tile(TcState& st, const CUtensorMap* mhi, const CUtensorMap* mlo, int V,
-                        int Nt, int Vp, int i0, int t0, int ns, const float2* in,
-                        const float2* cis, float scale, float inv_scale, Epi& epi) {
+                        int Nt, int Vp, int i0, int t0, int ns, const Src& src, float scale,
+                        float inv_scale, Epi& epi) {
     TileSmem& sm = *st.sm;
-    const int tid = threadIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = Vp / KCH;
     const int N = ((2 * ns + 15) / 16) * 16;
-    const uint32_t idesc = idesc_f16(TM, N);
-    const uint32_t tmem = sm.tmem_base;
-    bool ok = true;
     const uint32_t g0 = st.gchunk;
+    bool ok = true;
 
-    auto fill = [&](int kc, uint32_t g) {
-        const int s = g & 1;
-        if (g >= 2 && ok) ok = mbar_wait(smem_u32(&sm.mma_bar[s]), ((g - 2) >> 1) & 1, st.status);
-        if (tid == 0 && ok) {
-            const uint32_t bar = smem_u32(&sm.tma_bar[s]);
-            mbar_arrive_expect_tx(bar, 2 * kATileBytes);
-            tma_load_2d(smem_u32(sm.a_hi[s]), mhi, kc * KCH, i0, bar);
-            tma_load_2d(smem_u32(sm.a_lo[s]), mlo, kc * KCH, i0, bar);
+    if (warp == kWarpTma) {
+        if (lane == 0) {
+            for (int kc = 0; kc < nk && ok; ++kc) {
+                const uint32_t g = g0 + kc, s = g % kStages, n = g / kStages;
+                if (n > 0) ok = mbar_wait(smem_u32(&sm.empty[s]), (n - 1) & 1, st.status);
+                if (!ok) break;
+                const uint32_t bar = smem_u32(&sm.full[s]);
+                mbar_arrive_expect_tx(bar, 2 * kATileBytes);
+                tma_load_2d(smem_u32(sm.a_hi[s]), mhi, kc * KCH, i0, bar);
+                tma_load_2d(smem_u32(sm.a_lo[s]), mlo, kc * KCH, i0, bar);
+            }
         }
-        if (ok)
-            build_B<DAG>(in, cis, V, Nt, t0, ns, N, kc * KCH, scale, sm.b_hi[s], sm.b_lo[s]);
-        fence_proxy_async();
-    };
-
-    fill(0, g0);
-    __syncthreads();
-    for (int kc = 0; kc < nk; ++kc) {
-        const uint32_t g = g0 + kc;
-        const int s = g & 1;
-        if (tid == 0 && ok) {
-            ok = mbar_wait(smem_u32(&sm.tma_bar[s]), (g >> 1) & 1, st.status);
-            if (ok) {
+    } else if (warp == kWarpMma) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_f16(TM, N);
+            const uint32_t tmem = sm.tmem_base;
+            for (int kc = 0; kc < nk && ok; ++kc) {
+                const uint32_t g = g0 + kc, s = g % kStages, n = g / kStages;
+                ok = mbar_wait(smem_u32(&sm.full[s]), n & 1, st.status);
+                if (!ok) break;
                 fence_after_sync();
                 const uint32_t ah = smem_u32(sm.a_hi[s]), al = smem_u32(sm.a_lo[s]);
                 const uint32_t bh = smem_u32(sm.b_hi[s]), bl = smem_u32(sm.b_lo[s]);
@@ -243,45 +319,70 @@ __device__ bool tc_tile(TcState& st, const CUtensorMap* mhi, const CUtensorMap* 
                     mma_f16(tmem + kCorrCol, desc_sw128(al + off), desc_sw128(bh + off), idesc,
                             1u);
                 }
-                mma_commit(smem_u32(&sm.mma_bar[s]));
+                mma_commit(smem_u32(&sm.empty[s]));
             }
+            mma_commit(smem_u32(&sm.acc_full));
         }
-        if (kc + 1 < nk) fill(kc + 1, g + 1);
-        __syncthreads();
-    }
-    st.gchunk = g0 + nk;
-    {
-        const uint32_t g = g0 + nk - 1;
-        if (ok) ok = mbar_wait(smem_u32(&sm.mma_bar[g & 1]), (g >> 1) & 1, st.status);
-    }
-    fence_after_sync();
-    // epilogue: warp w reads TMEM lanes 32*(w%4).., column blocks of 16
-    const int warp = tid >> 5, lane = tid & 31;
-    const int row = (warp & 3) * 32 + lane;
-    const int i = i0 + row;
-    const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-    if (ok) {
-        for (int cb = (warp >> 2) * 16; cb < N; cb += 32) {
-            float m[16], c[16];
-            tmem_ld16(tl + cb, m);
-            tmem_ld16(tl + kCorrCol + cb, c);
-            if (i < V) {
+    } else {
+        // B producers (warps 2..7)
+        const int ptid = threadIdx.x - kFirstBWarp * 32, nprod = kNumBWarps * 32;
+        for (int kc = 0; kc < nk && ok; ++kc) {
+            const uint32_t g = g0 + kc, s = g % kStages, n = g / kStages;
+            if (n > 0) ok = mbar_wait(smem_u32(&sm.empty[s]), (n - 1) & 1, st.status);
+            if (!ok) break;
+            build_B<DAG>(src, V, Nt, t0, ns, N, kc * KCH, scale, sm.b_hi[s], sm.b_lo[s], ptid,
+                         nprod);
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
+                                            smem_u32(&sm.full[s]))
+                                        : "memory");
+        }
+        // epilogue on warps 4..7: lane quarter (warp % 4) of TMEM, all columns.
+        // The inputs of a block of 8 slices are fetched together (the first
+        // block before the accumulator is ready, overlapping the MMA tail).
+        if (warp >= kFirstEpiWarp) {
+            using In = typename Epi::In;
+            const int row = (warp & 3) * 32 + lane;
+            const int i = i0 + row;
+            In cur[8];
+            auto fetch = [&](int cb, In (&dst)[8]) {
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     const int tt = (cb >> 1) + e;
-                    if (tt < ns) {
-                        const float wr = fmaf(c[2 * e], kLoInv, m[2 * e]) * inv_scale;
-                        const float wi = fmaf(c[2 * e + 1], kLoInv, m[2 * e + 1]) * inv_scale;
-                        epi(i, t0 + tt, make_float2(wr, wi));
+                    if (i < V && tt < ns) dst[e] = epi.load(i, t0 + tt);
+                }
+            };
+            if (ok) fetch(0, cur);
+            if (ok) ok = mbar_wait(smem_u32(&sm.acc_full), st.ntile & 1, st.status);
+            fence_after_sync();
+            ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld below is warp-collective
+            if (ok) {
+                const uint32_t tl = sm.tmem_base + ((uint32_t)((warp & 3) * 32) << 16);
+                for (int cb = 0; cb < N; cb += 16) {
+                    if (cb > 0) fetch(cb, cur);
+                    float m[16], c[16];
+                    tmem_ld16(tl + cb, m);
+                    tmem_ld16(tl + kCorrCol + cb, c);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int tt = (cb >> 1) + e;
+                        if (i < V && tt < ns) {
+                            const float wr = fmaf(c[2 * e], kLoInv, m[2 * e]) * inv_scale;
+                            const float wi = fmaf(c[2 * e + 1], kLoInv, m[2 * e + 1]) * inv_scale;
+                            epi.store(i, t0 + tt, cur[e], make_float2(wr, wi));
+                        }
                     }
                 }
             }
         }
     }
+    st.gchunk = g0 + nk;
+    st.ntile += 1;
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-    return ok && (*((volatile int*)st.status) == 0);
+    return *((volatile int*)st.status) == 0;
 }
 
 }  // namespace tc

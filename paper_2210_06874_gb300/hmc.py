@@ -46,7 +46,8 @@ class hmc_params(ctypes.Structure):
                 ("U", ctypes.c_double), ("beta", ctypes.c_double), ("n_md", ctypes.c_int),
                 ("traj_length", ctypes.c_double), ("cg_tol", ctypes.c_double),
                 ("cg_max_iter", ctypes.c_int), ("precision", ctypes.c_int),
-                ("ru_delta", ctypes.c_double)]
+                ("ru_delta", ctypes.c_double), ("team_ctas", ctypes.c_int),
+                ("tile_slices", ctypes.c_int), ("inner_ctas", ctypes.c_int)]
 
 
 class hmc_cg_stats(ctypes.Structure):
@@ -130,6 +131,9 @@ class Params:
     cg_max_iter: int = 100000
     precision: int = PREC_FP64
     ru_delta: float = 0.0
+    team_ctas: int = 0
+    tile_slices: int = 0
+    inner_ctas: int = 0
 
     @property
     def V(self):
@@ -142,7 +146,8 @@ class Params:
     def to_c(self):
         return hmc_params(self.L, self.Nt, self.kappa, self.U, self.beta, self.n_md,
                           self.traj_length, self.cg_tol, self.cg_max_iter, self.precision,
-                          self.ru_delta)
+                          self.ru_delta, self.team_ctas, self.tile_slices,
+                          self.inner_ctas)
 
 
 class Context:

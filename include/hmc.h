@@ -148,6 +148,14 @@ int hmc_cg_solve(hmc_ctx* ctx, const double* phi, const void* chi, void* x,
  * Asynchronous. */
 int hmc_force(hmc_ctx* ctx, const double* phi, const void* x, double* F, void* stream);
 
+/* S = sum(phi^2) / (2 delta U) + Re(chi^dag x): the action of Eq. (2.1)
+ * without the momenta, given x = (M M^dag)^{-1} chi from hmc_cg_solve (so
+ * the second term is chi^dag (M M^dag)^{-1} chi).  Deterministic FP64
+ * reduction; *S_host is a host pointer and the call synchronises `stream`.
+ * Returns HMC_ERR_NONFINITE if S is not finite. */
+int hmc_action(hmc_ctx* ctx, const double* phi, const void* chi, const void* x, double* S_host,
+               void* stream);
+
 /* One HMC trajectory (§2) on device field phi (in/out, double [Nt][V]):
  * momenta pi ~ exp(-pi^2/2) and noise rho ~ exp(-rho^dag rho) from Philox
  * streams (seed, traj_index, chain), chi = M rho, leapfrog of n_md steps
@@ -157,6 +165,31 @@ int hmc_force(hmc_ctx* ctx, const double* phi, const void* x, double* F, void* s
  * stream synchronised.  Precision: params.precision. */
 int hmc_trajectory(hmc_ctx* ctx, double* phi, uint64_t seed, uint64_t traj_index,
                    uint32_t chain, hmc_traj_out* out, void* stream);
+
+/* ---- Batched chains ----------------------------------------------------
+ * Many independent Markov chains, each with its own hmc_params (lattice
+ * size, Nt, U, beta, ...), advanced together: one persistent launch where
+ * every CTA takes the next chain from a work queue (largest first) and runs
+ * its whole trajectory with the MIXED path (HMC_PREC_MIXED required; other
+ * precisions return HMC_ERR_UNSUPPORTED).  Chains with equal L and
+ * delta*kappa share E.  The launch is captured once into a CUDA graph on
+ * the batch's own stream and replayed; it is ordered after `stream`.
+ * Chain i uses Philox chain id i. */
+typedef struct hmc_batch hmc_batch;
+
+/* params: host array of n_chains parameter sets. */
+int hmc_batch_create(const hmc_params* params, int n_chains, hmc_batch** out);
+int hmc_batch_destroy(hmc_batch* batch);
+
+/* Packed field layout: chain i occupies phi[offsets[i] .. offsets[i+1]) as
+ * double [Nt_i][V_i]; offsets (host, n_offsets >= n_chains + 1) is filled. */
+int hmc_batch_layout(const hmc_batch* batch, int64_t* offsets, int n_offsets);
+
+/* One trajectory of every chain on the packed device field phi (in/out).
+ * out: host array of n_chains records; the call synchronises.  Returns the
+ * first non-OK chain status (each record carries its own). */
+int hmc_batch_trajectory(hmc_batch* batch, double* phi, uint64_t seed, uint64_t traj_index,
+                         hmc_traj_out* out, void* stream);
 
 /* Philox4x32-10 draws of the library's streams, for checking the generator
  * (Salmon et al., SC'11): element e of stream `stream_id` for

@@ -9,4 +9,4 @@ synthetic inputs; `autograd` wraps the adjoint force as a
 torch.autograd.Function.  Importing the package does not load the library;
 the first use of `hmc` does, and fails loudly if it has not been built.
 """
-__all__ = ["hmc", "synth", "build_lib"]
+__all__ = ["hmc", "synth", "build_lib", "autograd"]

@@ -303,6 +303,20 @@ int hmc_force(hmc_ctx* c, const double* phi, const void* x, double* F, void* str
     return launch_force_f64(c->view, phi, (const double2*)x, F, s);
 }
 
+int hmc_action(hmc_ctx* c, const double* phi, const void* chi, const void* x, double* S_host,
+               void* stream) {
+    if (!c || !phi || !chi || !x || !S_host) return HMC_ERR_BAD_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = launch_action(c->view, phi, (const double2*)chi, (const double2*)x, c->view.scalars, s);
+    if (st != HMC_OK) return st;
+    if (cudaMemcpyAsync(c->scalars_host, c->view.scalars, sizeof(double), cudaMemcpyDeviceToHost,
+                        s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return HMC_ERR_CUDA;
+    *S_host = c->scalars_host[0];
+    return std::isfinite(*S_host) ? HMC_OK : HMC_ERR_NONFINITE;
+}
+
 int hmc_trajectory(hmc_ctx* c, double* phi, uint64_t seed, uint64_t traj_index, uint32_t chain,
                    hmc_traj_out* out, void* stream) {
     if (!c || !phi || !out) return HMC_ERR_BAD_ARG;

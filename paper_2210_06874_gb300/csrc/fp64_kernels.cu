@@ -55,6 +55,28 @@ __device__ __forceinline__ void fill_cis(const ChainView& c, const Team& tm, con
     }
 }
 
+// Action Eq. (2.1) without the momenta: per-CTA partials of
+// sum(phi^2) / (2 delta U) + Re(chi^dag x), then a one-CTA fixed-order sum.
+__global__ void k_action_partials(const double* __restrict__ phi, const double2* __restrict__ chi,
+                                  const double2* __restrict__ x, int N, double half_inv_dU,
+                                  double* __restrict__ partials) {
+    double v[1] = {0.0};
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < N; e += gridDim.x * blockDim.x) {
+        const double ph = phi[e];
+        const double2 a = chi[e], b = x[e];
+        v[0] += half_inv_dU * ph * ph + a.x * b.x + a.y * b.y;
+    }
+    block_reduce<1>(v);
+    if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
+}
+
+__global__ void k_sum_partials(const double* __restrict__ partials, int n, double* out) {
+    double v[1] = {0.0};
+    for (int j = threadIdx.x; j < n; j += blockDim.x) v[0] += partials[j];
+    block_reduce<1>(v);
+    if (threadIdx.x == 0) *out = v[0];
+}
+
 // scalars: [0] iterations [1] true residual [2] status
 __global__ void __launch_bounds__(NTHR) k_cg(ChainView c, const double* phi, const double2* chi,
                                              double2* x, double tol, int max_iter) {
@@ -201,6 +223,16 @@ int launch_force_f64(const ChainView& c, const double* phi, const double2* x, do
                      cudaStream_t s) {
     const int nt = ((c.V + f64::TI - 1) / f64::TI) * ((c.Nt + f64::TT - 1) / f64::TT);
     f64::k_force<<<nt, f64::NTHR, 0, s>>>(c, phi, x, F);
+    return cudaGetLastError() == cudaSuccess ? HMC_OK : HMC_ERR_CUDA;
+}
+
+int launch_action(const ChainView& c, const double* phi, const double2* chi, const double2* x,
+                  double* out, cudaStream_t s) {
+    int blocks = (c.N + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    f64::k_action_partials<<<blocks, 256, 0, s>>>(phi, chi, x, c.N, 0.5 / (c.delta * c.U),
+                                                 c.partials);
+    f64::k_sum_partials<<<1, 256, 0, s>>>(c.partials, blocks, out);
     return cudaGetLastError() == cudaSuccess ? HMC_OK : HMC_ERR_CUDA;
 }
 

@@ -31,6 +31,8 @@ int launch_apply_f64(const ChainView& c, bool dag, const double2* in, double2* o
                      cudaStream_t s);
 int launch_force_f64(const ChainView& c, const double* phi, const double2* x, double* F,
                      cudaStream_t s);
+int launch_action(const ChainView& c, const double* phi, const double2* chi, const double2* x,
+                  double* out, cudaStream_t s);
 int launch_cg_f64(const ChainView& c, int num_sms, const double* phi, const double2* chi,
                   double2* x, double tol, int max_iter, cudaStream_t s);
 int launch_trajectory_f64(const ChainView& c, int num_sms, const TrajArgs& a, cudaStream_t s);

@@ -5,7 +5,9 @@
 #include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "fp64_path.cuh"
@@ -217,6 +219,20 @@ struct PersistentArgs {
     double ru_delta;
 };
 
+struct BatchItem {
+    ChainView v;
+    const CUtensorMap* maps;   // [0] E_hi, [1] E_lo (global memory, 64-byte aligned)
+    PersistentArgs pa;
+    TrajArgs a;                // n_md, eps, tol, max_iter, chain; seed/traj/phi per call
+    long long offset;          // of this chain's field in the packed array
+};
+
+struct BatchCallArgs {
+    uint64_t seed;
+    uint64_t traj;
+    double* phi;               // packed fields of all chains
+};
+
 // FP64 true residual of x64: r64 = chi - M (M^dag x64); returns |r64|^2.
 __device__ bool f64_residual(const ChainView& c, Team& tm, f64::Smem& sm, const double2* chi,
                              double2* x64, double& rr) {
@@ -404,16 +420,11 @@ __global__ void __launch_bounds__(NTHR, 1)
     tc_teardown(st);
 }
 
-// One HMC trajectory with the mixed solver (same steps as the FP64 one).
-__global__ void __launch_bounds__(NTHR, 1)
-    k_trajectory(const __grid_constant__ CUtensorMap mhi,
-                 const __grid_constant__ CUtensorMap mlo, ChainView c, PersistentArgs pa,
-                 TrajArgs a) {
-    extern __shared__ __align__(1024) uint8_t dyn[];
-    __shared__ f64::Smem sm64;
-    TcState st;
-    tc_setup(st, dyn, c.status);
-    Team tm = make_team(c);
+// One HMC trajectory with the mixed solver (same steps as the FP64 one),
+// run by team `tm`; results in c.scalars.  Returns false if the team failed.
+__device__ bool run_trajectory(const ChainView& c, Team& tm, TcState& st, f64::Smem& sm64,
+                               const CUtensorMap* mhi, const CUtensorMap* mlo,
+                               const PersistentArgs& pa, const TrajArgs& a) {
     double* phi = a.phi;
     const double inv_dU = 1.0 / (c.delta * c.U);
     const double rsqrt2 = 0.70710678118654752440;
@@ -460,7 +471,7 @@ __global__ void __launch_bounds__(NTHR, 1)
             if (!(ok = team_barrier(tm))) break;
         }
         MixedResult res{};
-        if (!(ok = cg_mixed(c, tm, st, sm64, &mhi, &mlo, pa, c.chi, c.x, res))) break;
+        if (!(ok = cg_mixed(c, tm, st, sm64, mhi, mlo, pa, c.chi, c.x, res))) break;
         iters += res.iterations;
         rus += res.reliable_updates;
         ++solves;
@@ -503,9 +514,73 @@ __global__ void __launch_bounds__(NTHR, 1)
             c.scalars[kTrajStatus] = status;
         }
     }
+    return ok;
+}
+
+__global__ void __launch_bounds__(NTHR, 1)
+    k_trajectory(const __grid_constant__ CUtensorMap mhi,
+                 const __grid_constant__ CUtensorMap mlo, ChainView c, PersistentArgs pa,
+                 TrajArgs a) {
+    extern __shared__ __align__(1024) uint8_t dyn[];
+    __shared__ f64::Smem sm64;
+    TcState st;
+    tc_setup(st, dyn, c.status);
+    Team tm = make_team(c);
+    run_trajectory(c, tm, st, sm64, &mhi, &mlo, pa, a);
     tc_teardown(st);
 }
 
+// ---------------------------------------------------------------- batched
+// Many independent chains of different sizes in one persistent launch: each
+// CTA takes the next chain from an atomic work queue (chains ordered by
+// decreasing estimated cost) and runs its whole trajectory as a one-CTA
+// team; the TMEM allocation and the operand ring persist across chains.
+__global__ void __launch_bounds__(NTHR, 1)
+    k_batch(const BatchItem* __restrict__ items, const int* __restrict__ order, int n,
+            int* queue, const BatchCallArgs* call, double* outs) {
+    extern __shared__ __align__(1024) uint8_t dyn[];
+    __shared__ f64::Smem sm64;
+    __shared__ int s_idx;
+    TcState st;
+    tc_setup(st, dyn, items[0].v.status);
+    for (;;) {
+        if (threadIdx.x == 0) s_idx = atomicAdd(queue, 1);
+        __syncthreads();
+        const int idx = s_idx;
+        __syncthreads();
+        if (idx >= n) break;
+        const int ci = order[idx];
+        const BatchItem& it = items[ci];
+        if (threadIdx.x == 0) {
+            *it.v.status = 0;
+            for (int k = 0; k < kNumScalars; ++k) it.v.scalars[k] = 0.0;
+        }
+        __syncthreads();
+        Team tm;
+        tm.rank = 0;
+        tm.size = 1;
+        tm.bar = it.v.bar;
+        tm.status = it.v.status;
+        tm.partials = it.v.partials;
+        tm.slot = 0;
+        st.status = it.v.status;
+        TrajArgs a = it.a;
+        a.seed = call->seed;
+        a.traj = call->traj;
+        a.phi = call->phi + it.offset;
+        const bool ok = run_trajectory(it.v, tm, st, sm64, it.maps, it.maps + 1, it.pa, a);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < kNumScalars; ++k) outs[(size_t)ci * kNumScalars + k] = it.v.scalars[k];
+            outs[(size_t)ci * kNumScalars + kTrajStatus] =
+                ok ? it.v.scalars[kTrajStatus] : (double)(*((volatile int*)it.v.status));
+        }
+        // a failed bounded wait leaves the operand ring in an unknown phase:
+        // this CTA takes no further chains (they stay unprocessed, status set)
+        if (!ok) break;
+    }
+    tc_teardown(st);
+}
 }  // namespace tc
 
 // ---------------------------------------------------------------- host side
@@ -681,6 +756,217 @@ int tc_trajectory(hmc_ctx* c, const TrajArgs& a, cudaStream_t s) {
                                        dim3(tc::NTHR), args, tc::kSmemBytes, s) == cudaSuccess
                ? HMC_OK
                : HMC_ERR_CUDA;
+}
+
+
+// ---------------------------------------------------------------- batch (host)
+struct TcBatch {
+    int n = 0;
+    int grid = 0;
+    std::vector<hmc_ctx*> ctxs;
+    std::vector<long long> offsets;   // n + 1
+    tc::BatchItem* d_items = nullptr;
+    int* d_order = nullptr;
+    int* d_queue = nullptr;
+    tc::BatchCallArgs* d_call = nullptr;
+    tc::BatchCallArgs* h_call = nullptr;   // pinned
+    double* d_outs = nullptr;
+    double* h_outs = nullptr;          // pinned
+    CUtensorMap* d_maps = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ready = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    double* graph_phi = nullptr;
+};
+
+void tc_batch_destroy(TcBatch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->ready) cudaEventDestroy(b->ready);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    cudaFree(b->d_items);
+    cudaFree(b->d_order);
+    cudaFree(b->d_queue);
+    cudaFree(b->d_call);
+    cudaFree(b->d_outs);
+    cudaFree(b->d_maps);
+    if (b->h_call) cudaFreeHost(b->h_call);
+    if (b->h_outs) cudaFreeHost(b->h_outs);
+    for (hmc_ctx* c : b->ctxs) hmc_ctx_destroy(c);
+    delete b;
+}
+
+int tc_batch_create(const hmc_params* p, int n, TcBatch** out) {
+    TcBatch* b = new TcBatch();
+    b->n = n;
+    int st = HMC_OK;
+    // one context per chain (workspaces); chains with the same lattice and
+    // delta*kappa share the first such context's E, its split and maps
+    std::vector<int> leader(n);
+    std::vector<int> map_slot(n);
+    int n_maps = 0;
+    for (int i = 0; i < n && st == HMC_OK; ++i) {
+        if (p[i].precision != HMC_PREC_MIXED) st = HMC_ERR_UNSUPPORTED;
+        hmc_ctx* c = nullptr;
+        if (st == HMC_OK) st = hmc_ctx_create(&p[i], &c);
+        if (st != HMC_OK) break;
+        b->ctxs.push_back(c);
+        leader[i] = i;
+        for (int j = 0; j < i; ++j)
+            if (p[j].L == p[i].L &&
+                p[j].beta / p[j].Nt * p[j].kappa == p[i].beta / p[i].Nt * p[i].kappa) {
+                leader[i] = leader[j];
+                break;
+            }
+        map_slot[i] = (leader[i] == i) ? n_maps++ : map_slot[leader[i]];
+    }
+    if (st != HMC_OK) {
+        tc_batch_destroy(b);
+        return st;
+    }
+    std::vector<CUtensorMap> maps(2 * n_maps);
+    for (int i = 0; i < n; ++i)
+        if (leader[i] == i) {
+            maps[2 * map_slot[i]] = b->ctxs[i]->tc->map_hi;
+            maps[2 * map_slot[i] + 1] = b->ctxs[i]->tc->map_lo;
+        }
+    std::vector<tc::BatchItem> items(n);
+    b->offsets.assign(n + 1, 0);
+    std::vector<double> cost(n);
+    for (int i = 0; i < n; ++i) {
+        hmc_ctx* c = b->ctxs[i];
+        const ChainView& lv = b->ctxs[leader[i]]->view;
+        tc::BatchItem& it = items[i];
+        it.v = c->view;
+        it.v.E = lv.E;
+        it.v.E_hi = lv.E_hi;
+        it.v.E_lo = lv.E_lo;
+        it.pa.inner = 1;
+        it.pa.ns_tile = pick_ns(it.v.Vr / tc::TM, it.v.Nt, 1);
+        if (c->params.tile_slices > 0) it.pa.ns_tile = c->params.tile_slices;
+        it.pa.tol = c->params.cg_tol;
+        it.pa.max_iter = c->params.cg_max_iter;
+        it.pa.ru_delta = c->params.ru_delta;
+        std::memset(&it.a, 0, sizeof(it.a));
+        it.a.chain = (uint32_t)i;
+        it.a.n_md = c->params.n_md;
+        it.a.eps = c->params.traj_length / c->params.n_md;
+        it.a.tol = c->params.cg_tol;
+        it.a.max_iter = c->params.cg_max_iter;
+        it.a.ru_delta = c->params.ru_delta;
+        it.offset = b->offsets[i];
+        b->offsets[i + 1] = b->offsets[i] + it.v.N;
+        // cost proxy: tile work of one application times Nt (CG iterations
+        // grow with beta = Nt * delta)
+        cost[i] = (double)it.v.Vr * it.v.Vp * it.v.Nt * it.v.Nt;
+    }
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int c) { return cost[a] > cost[c]; });
+    bool ok = true;
+    auto alloc = [&](void** ptr, size_t bytes) {
+        if (ok && cudaMalloc(ptr, bytes) != cudaSuccess) ok = false;
+    };
+    alloc((void**)&b->d_maps, sizeof(CUtensorMap) * maps.size());
+    alloc((void**)&b->d_items, sizeof(tc::BatchItem) * n);
+    alloc((void**)&b->d_order, sizeof(int) * n);
+    alloc((void**)&b->d_queue, sizeof(int));
+    alloc((void**)&b->d_call, sizeof(tc::BatchCallArgs));
+    alloc((void**)&b->d_outs, sizeof(double) * kNumScalars * n);
+    if (ok && (cudaMallocHost((void**)&b->h_call, sizeof(tc::BatchCallArgs)) != cudaSuccess ||
+               cudaMallocHost((void**)&b->h_outs, sizeof(double) * kNumScalars * n) !=
+                   cudaSuccess))
+        ok = false;
+    if (ok) {
+        for (int i = 0; i < n; ++i) items[i].maps = b->d_maps + 2 * map_slot[i];
+        ok = cudaMemcpy(b->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                        cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(b->d_items, items.data(), sizeof(tc::BatchItem) * n,
+                        cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(b->d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice) ==
+                 cudaSuccess &&
+             cudaFuncSetAttribute((const void*)tc::k_batch,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)tc::kSmemBytes) == cudaSuccess &&
+             cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&b->ready, cudaEventDisableTiming) == cudaSuccess;
+    }
+    int occ = 0;
+    if (ok && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)tc::k_batch,
+                                                             tc::NTHR, tc::kSmemBytes) !=
+                   cudaSuccess ||
+               occ < 1))
+        ok = false;
+    if (!ok) {
+        tc_batch_destroy(b);
+        return HMC_ERR_CUDA;
+    }
+    b->grid = std::min(n, b->ctxs[0]->num_sms * occ);
+    *out = b;
+    return HMC_OK;
+}
+
+void tc_batch_offsets(const TcBatch* b, long long* off) {
+    for (int i = 0; i <= b->n; ++i) off[i] = b->offsets[i];
+}
+
+int tc_batch_size(const TcBatch* b) { return b->n; }
+
+// One trajectory of every chain: the launch is captured once into a CUDA
+// graph on the batch's own stream (H2D of the call arguments from pinned
+// memory, queue reset, the persistent kernel, D2H of the results) and
+// replayed; it is ordered after the caller's stream by an event.
+int tc_batch_trajectory(TcBatch* b, double* phi, uint64_t seed, uint64_t traj,
+                        hmc_traj_out* out, cudaStream_t caller) {
+    if (!b->exec || b->graph_phi != phi) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+        cudaStream_t s = b->stream;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return HMC_ERR_CUDA;
+        cudaMemcpyAsync(b->d_call, b->h_call, sizeof(tc::BatchCallArgs), cudaMemcpyHostToDevice, s);
+        cudaMemsetAsync(b->d_queue, 0, sizeof(int), s);
+        tc::k_batch<<<b->grid, tc::NTHR, tc::kSmemBytes, s>>>(b->d_items, b->d_order, b->n,
+                                                            b->d_queue, b->d_call, b->d_outs);
+        cudaMemcpyAsync(b->h_outs, b->d_outs, sizeof(double) * kNumScalars * b->n,
+                        cudaMemcpyDeviceToHost, s);
+        if (cudaStreamEndCapture(s, &b->graph) != cudaSuccess ||
+            cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess)
+            return HMC_ERR_CUDA;
+        b->graph_phi = phi;
+    }
+    b->h_call->seed = seed;
+    b->h_call->traj = traj;
+    b->h_call->phi = phi;
+    if (cudaEventRecord(b->ready, caller) != cudaSuccess ||
+        cudaStreamWaitEvent(b->stream, b->ready, 0) != cudaSuccess ||
+        cudaGraphLaunch(b->exec, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return HMC_ERR_CUDA;
+    int first_bad = HMC_OK;
+    for (int i = 0; i < b->n; ++i) {
+        const double* v = b->h_outs + (size_t)i * kNumScalars;
+        hmc_traj_out& o = out[i];
+        o.dH = v[kTrajDH];
+        o.H0 = v[kTrajH0];
+        o.H1 = v[kTrajH1];
+        o.u = v[kTrajU];
+        o.accept = (int)v[kTrajAccept];
+        o.cg_iterations = (int)v[kTrajIters];
+        o.cg_solves = (int)v[kTrajSolves];
+        o.reliable_updates = (int)v[kTrajRU];
+        o.max_true_residual = v[kTrajMaxRes];
+        o.status = (int)v[kTrajStatus];
+        if (o.cg_solves == 0 && o.status == HMC_OK) o.status = HMC_ERR_TIMEOUT;  // not run
+        if (o.status != HMC_OK && first_bad == HMC_OK) first_bad = o.status;
+    }
+    return first_bad;
 }
 
 }  // namespace hmc

@@ -16,4 +16,12 @@ int tc_cg(hmc_ctx* c, const double* phi, const double2* chi, double2* x, double 
           int max_iter, cudaStream_t s);
 int tc_trajectory(hmc_ctx* c, const TrajArgs& a, cudaStream_t s);
 
+struct TcBatch;
+int tc_batch_create(const hmc_params* p, int n, TcBatch** out);
+void tc_batch_destroy(TcBatch* b);
+void tc_batch_offsets(const TcBatch* b, long long* off);
+int tc_batch_size(const TcBatch* b);
+int tc_batch_trajectory(TcBatch* b, double* phi, uint64_t seed, uint64_t traj,
+                        hmc_traj_out* out, cudaStream_t caller);
+
 }  // namespace hmc

@@ -76,11 +76,18 @@ SIGNATURES = {
     "hmc_cg_solve": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_double, ctypes.c_int,
                                     ctypes.c_int, ctypes.POINTER(hmc_cg_stats), _P]),
     "hmc_force": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "hmc_action": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double), _P]),
     "hmc_trajectory": (ctypes.c_int, [_P, _P, ctypes.c_uint64, ctypes.c_uint64,
                                       ctypes.c_uint32, ctypes.POINTER(hmc_traj_out), _P]),
     "hmc_rng_draw": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
                                     ctypes.c_uint32, ctypes.c_int64, _P, _P, _P, _P]),
     "hmc_version": (ctypes.c_char_p, []),
+    "hmc_batch_create": (ctypes.c_int, [ctypes.POINTER(hmc_params), ctypes.c_int,
+                                        ctypes.POINTER(_P)]),
+    "hmc_batch_destroy": (ctypes.c_int, [_P]),
+    "hmc_batch_layout": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.c_int]),
+    "hmc_batch_trajectory": (ctypes.c_int, [_P, _P, ctypes.c_uint64, ctypes.c_uint64,
+                                            ctypes.POINTER(hmc_traj_out), _P]),
     "hmc_cg_solve_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P,
                                             ctypes.c_double, ctypes.c_int,
                                             ctypes.POINTER(hmc_cg_stats), _P]),
@@ -235,6 +242,16 @@ class Context:
         _check("hmc_force", self.lib.hmc_force(self._h, _ptr(phi), _ptr(x), _ptr(F), _stream()))
         return F
 
+    def action(self, phi, chi, x):
+        """S = sum(phi^2)/(2 delta U) + Re(chi^dag x) (FP64, host float)."""
+        self._field(phi, "phi", torch.float64)
+        self._field(chi, "chi", torch.complex128)
+        self._field(x, "x", torch.complex128)
+        out = ctypes.c_double()
+        _check("hmc_action", self.lib.hmc_action(self._h, _ptr(phi), _ptr(chi), _ptr(x),
+                                                 ctypes.byref(out), _stream()))
+        return out.value
+
     def trajectory(self, phi, seed, traj_index, chain=0, allow_not_converged=False):
         self._field(phi, "phi", torch.float64)
         out = hmc_traj_out()
@@ -243,6 +260,57 @@ class Context:
                                                          chain, ctypes.byref(out), _stream()),
                allow)
         return out
+
+
+class Batch:
+    """Many independent chains (one hmc_params each, MIXED precision) advanced
+    by one persistent launch per trajectory (hmc_batch_*)."""
+
+    def __init__(self, params_list):
+        self.lib = load_library()
+        self.params = list(params_list)
+        self.n = len(self.params)
+        arr = (hmc_params * self.n)(*[p.to_c() for p in self.params])
+        h = ctypes.c_void_p()
+        _check("hmc_batch_create", self.lib.hmc_batch_create(arr, self.n, ctypes.byref(h)))
+        self._h = h
+        off = (ctypes.c_int64 * (self.n + 1))()
+        _check("hmc_batch_layout", self.lib.hmc_batch_layout(self._h, off, self.n + 1))
+        self.offsets = [int(v) for v in off]
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self.lib.hmc_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def total(self):
+        return self.offsets[-1]
+
+    def view(self, phi, i):
+        """Chain i's field [Nt, V] inside the packed tensor phi."""
+        p = self.params[i]
+        return phi[self.offsets[i]:self.offsets[i + 1]].view(p.Nt, p.V)
+
+    def trajectory(self, phi, seed, traj_index, allow_failure=False):
+        if not isinstance(phi, torch.Tensor) or phi.dtype != torch.float64 or \
+                phi.device != self.device or phi.numel() != self.total or \
+                not phi.is_contiguous():
+            raise ValueError("phi must be a contiguous float64 tensor of %d elements on %s"
+                             % (self.total, self.device))
+        outs = (hmc_traj_out * self.n)()
+        code = self.lib.hmc_batch_trajectory(self._h, _ptr(phi), seed, traj_index, outs,
+                                             _stream())
+        if not allow_failure:
+            _check("hmc_batch_trajectory", code)
+        return list(outs)
 
 
 def rng_draw(seed, stream_id, traj, chain, n, device=None):

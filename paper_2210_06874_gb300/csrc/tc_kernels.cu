@@ -554,6 +554,13 @@ __global__ void __launch_bounds__(NTHR, 1)
         if (threadIdx.x == 0) {
             *it.v.status = 0;
             for (int k = 0; k < kNumScalars; ++k) it.v.scalars[k] = 0.0;
+            // the maps live in global memory: make them visible to the TMA
+            // (async) proxy of the thread that issues the tile loads
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(it.maps)
+                         : "memory");
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                             it.maps + 1)
+                         : "memory");
         }
         __syncthreads();
         Team tm;

@@ -42,6 +42,9 @@ def parse():
                     help="trajectory: HMC trajectories/s; apply: M-applications/s")
     ap.add_argument("--applies", type=int, default=20,
                     help="apply mode: applications of M per step")
+    ap.add_argument("--chains", type=int, default=256, help="batch workload: chains")
+    ap.add_argument("--loop-chains", type=int, default=32,
+                    help="batch workload: chains timed as a loop of single-chain launches")
     ap.add_argument("--therm", type=int, default=None,
                     help="untimed thermalisation trajectories before warm-up")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -424,8 +427,104 @@ def run_apply(args):
         print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """Config 4: many chains of uneven size, one persistent launch per
+    trajectory of every chain (hmc_batch_trajectory); value = aggregate
+    trajectories/s.  Also times the same chains as a loop of single-chain
+    hmc_trajectory launches (each using the whole GPU)."""
+    import torch
+    from paper_2210_06874_gb300 import build_lib, hmc, synth
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    build_lib.build()
+    n = args.chains
+    specs = synth.batch256(n_chains=n)
+    plist = [hmc.Params(L=c["L"], Nt=c["Nt"], kappa=c["kappa"], U=c["U"], beta=c["beta"],
+                        n_md=c["n_md"], traj_length=c["traj_length"], cg_tol=c["cg_tol"],
+                        cg_max_iter=200000, precision=hmc.PREC_MIXED) for c in specs]
+    b = hmc.Batch(plist)
+    dev = torch.device("cuda", local_rank)
+    phi = torch.zeros(b.total, dtype=torch.float64, device=dev)   # cold start
+    seed = synth.BASE_SEED + 3 + 1000 * rank
+    traj = 0
+    n_therm = args.therm if args.therm is not None else 2
+    for _ in range(n_therm + args.warmup):
+        b.trajectory(phi, seed, traj, allow_failure=True)
+        traj += 1
+    clocks = ClockSampler(local_rank)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    clocks.start()
+    total_ms, outs = 0.0, []
+    for _ in range(args.steps):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        o = b.trajectory(phi, seed, traj, allow_failure=True)
+        e.record(stream)
+        e.synchronize()
+        total_ms += s.elapsed_time(e)
+        outs.extend(o)
+        traj += 1
+    clk = clocks.stop()
+    value = world * n * args.steps / (total_ms * 1e-3)
+    # loop of single-chain launches over the same chains (first K_loop chains)
+    n_loop = min(n, args.loop_chains)
+    loop_ms = 0.0
+    if n_loop > 0:
+        ctxs = [hmc.Context(p) for p in plist[:n_loop]]
+        fields = [b.view(phi, i).clone() for i in range(n_loop)]
+        for i, c in enumerate(ctxs):
+            c.trajectory(fields[i], seed, traj, chain=i, allow_not_converged=True)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        for i, c in enumerate(ctxs):
+            c.trajectory(fields[i], seed, traj + 1, chain=i, allow_not_converged=True)
+        e.record(stream)
+        e.synchronize()
+        loop_ms = s.elapsed_time(e)
+    sizes = [(p.L, p.Nt) for p in plist]
+    flop = sum((applies_per_traj(o, plist[i % n].n_md)) * flops_per_apply(plist[i % n].V,
+                                                                         plist[i % n].Nt)
+               for i, o in enumerate(outs)) / args.steps
+    peaks, kind = load_peaks()
+    peak = peaks.get("bf16_tflops_sustained", FALLBACK["bf16_tflops_sustained"])
+    achieved = flop / (total_ms / args.steps * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "trajectories/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f16-split/f32 (f64 residuals)", "data": "synthetic",
+        "config": {"workload": "batch%d" % n, "precision": "mixed", "chains": n,
+                   "L_set": sorted(set(p.L for p in plist)),
+                   "Nt_set": sorted(set(p.Nt for p in plist)),
+                   "thermalisation_trajectories": n_therm,
+                   "step": "one trajectory of every chain in one persistent launch (CUDA graph)",
+                   "l2": "inputs (all chains' fields and workspaces) exceed one trajectory's "
+                         "reuse window; no flush"},
+        "loop_of_single_chain_launches": {
+            "chains": n_loop, "ms": loop_ms,
+            "trajectories_per_s": n_loop / (loop_ms * 1e-3) if loop_ms else None},
+        "acceptance": statistics.mean(o.accept for o in outs),
+        "cg_iterations_per_traj": statistics.mean(o.cg_iterations for o in outs),
+        "max_true_residual": max(o.max_true_residual for o in outs),
+        "statuses": sorted(set(o.status for o in outs)),
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": "%s bf16 dense sustained (fp16 has the same rate)" % kind},
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload.startswith("batch") and args.impl == "ours":
+        run_batch(args)
+        return
     if args.mode == "apply" and args.impl == "ours":
         run_apply(args)
         return

@@ -52,6 +52,19 @@ def parse():
     return ap.parse_args()
 
 
+def aggregate_rate(local_ms, units_per_rank, world, dist=None, device=None):
+    """Whole-job rate of independent replicas: every rank processed
+    units_per_rank units; the job took the slowest rank's time (max over
+    ranks).  Returns (units per second over all ranks, max ms)."""
+    ms = float(local_ms)
+    if world > 1:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * units_per_rank / (ms * 1e-3), ms
+
+
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
             int(os.environ.get("WORLD_SIZE", "1")))
@@ -268,13 +281,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
+    value, total_ms = aggregate_rate(total_ms, args.steps, world, dist, dev)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms * 1e-3)
 
     # end to end through the public API with host buffers: pinned phi in,
     # trajectory, phi and the trajectory record back to the host

@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--therm", type=int, default=None,
                     help="untimed thermalisation trajectories before warm-up")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     return ap.parse_args()
 
@@ -249,6 +250,12 @@ def run_ours(args):
     build_lib.build()
     name = args.workload
     w, params, prec = workload_params(name, args.precision)
+    tuned = None
+    if prec == "mixed" and not args.no_tune:
+        from paper_2210_06874_gb300 import autotune
+        params = autotune.tune(params)
+        tuned = {"team_ctas": params.team_ctas, "inner_ctas": params.inner_ctas,
+                 "tile_slices": params.tile_slices}
     ctx = hmc.Context(params)
     V, Nt = params.V, params.Nt
     dev = torch.device("cuda", local_rank)
@@ -334,7 +341,8 @@ def run_ours(args):
                    "U": w["U"], "beta": w["beta"], "n_md": params.n_md,
                    "cg_tol": params.cg_tol, "thermalisation_trajectories": n_therm,
                    "l2": "flushed (256 MB write) between timed trajectories",
-                   "parallelism": "replicas (one chain per GPU)"},
+                   "parallelism": "replicas (one chain per GPU)",
+                   "launch_shape": tuned or "automatic"},
         "m_applications_per_s": world * n_app / (ms_per_step * 1e-3),
         "cg_iterations_per_traj": mean_iters,
         "acceptance": statistics.mean(o.accept for o in outs),
@@ -453,6 +461,16 @@ def run_batch(args):
     plist = [hmc.Params(L=c["L"], Nt=c["Nt"], kappa=c["kappa"], U=c["U"], beta=c["beta"],
                         n_md=c["n_md"], traj_length=c["traj_length"], cg_tol=c["cg_tol"],
                         cg_max_iter=200000, precision=hmc.PREC_MIXED) for c in specs]
+    shapes = {}
+    if not args.no_tune:
+        from paper_2210_06874_gb300 import autotune
+        tuned = [autotune.tune(p, single_cta=True) for p in plist]
+        for p in tuned:
+            shapes["L%d_Nt%d" % (p.L, p.Nt)] = p.tile_slices
+        loop_params = [autotune.tune(p) for p in plist[:args.loop_chains]]
+        plist = tuned
+    else:
+        loop_params = plist[:args.loop_chains]
     b = hmc.Batch(plist)
     dev = torch.device("cuda", local_rank)
     phi = torch.zeros(b.total, dtype=torch.float64, device=dev)   # cold start
@@ -482,7 +500,7 @@ def run_batch(args):
     n_loop = min(n, args.loop_chains)
     loop_ms = 0.0
     if n_loop > 0:
-        ctxs = [hmc.Context(p) for p in plist[:n_loop]]
+        ctxs = [hmc.Context(p) for p in loop_params[:n_loop]]
         fields = [b.view(phi, i).clone() for i in range(n_loop)]
         for i, c in enumerate(ctxs):
             c.trajectory(fields[i], seed, traj, chain=i, allow_not_converged=True)
@@ -511,6 +529,7 @@ def run_batch(args):
                    "Nt_set": sorted(set(p.Nt for p in plist)),
                    "thermalisation_trajectories": n_therm,
                    "step": "one trajectory of every chain in one persistent launch (CUDA graph)",
+                   "tile_slices_by_autotuner": shapes or "automatic",
                    "l2": "inputs (all chains' fields and workspaces) exceed one trajectory's "
                          "reuse window; no flush"},
         "loop_of_single_chain_launches": {

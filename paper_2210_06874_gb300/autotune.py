@@ -1,0 +1,77 @@
+"""Autotuner for the launch shape of the mixed-precision path.
+
+For one chain it times short mixed CG solves with a fixed iteration count
+(max_iter iterations, convergence not required: the per-iteration cost does
+not depend on the residual) for candidate shapes -- CTAs of the persistent
+launch (team_ctas), CTAs of the FP32 inner loop (inner_ctas), time slices per
+tensor-core tile (tile_slices) -- and keeps the fastest.  Timing uses CUDA
+events on the current stream around calls through the C ABI; results are
+cached per (L, Nt, team constraint) for the process.
+"""
+import itertools
+
+import torch
+
+from . import hmc
+
+_cache = {}
+
+
+def candidates(params, num_sms, single_cta=False):
+    """Shapes worth timing for this lattice: one CTA, or teams sized to the
+    number of tensor-core tiles / FP64 tiles at each tile width."""
+    V, Nt = params.V, params.Nt
+    nti = (V + 127) // 128
+    f64_tiles = ((V + 31) // 32) * ((Nt + 7) // 8)
+    out = []
+    for ns in (8, 16, 32):
+        tiles = nti * ((Nt + ns - 1) // ns)
+        if single_cta:
+            out.append((1, 1, ns))
+            continue
+        for inner in sorted({1, min(tiles, num_sms)}):
+            for team in sorted({max(inner, min(f64_tiles, num_sms)), min(num_sms, max(inner, 1))}):
+                out.append((team, inner, ns))
+    return sorted(set(out))
+
+
+def pick(timings):
+    """(shape, seconds per iteration) pairs -> fastest shape (ties: fewer CTAs)."""
+    return min(timings, key=lambda kv: (kv[1], kv[0][0], kv[0][1], kv[0][2]))[0]
+
+
+def tune(params, iters=40, reps=2, single_cta=False, seed=1):
+    """Return a copy of params with team_ctas, inner_ctas and tile_slices set
+    to the fastest measured shape."""
+    key = (params.L, params.Nt, round(params.beta / params.Nt, 12), single_cta)
+    if key in _cache:
+        team, inner, ns = _cache[key]
+    else:
+        dev = torch.device("cuda", torch.cuda.current_device())
+        num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        V, Nt = params.V, params.Nt
+        phi = (0.3 * torch.randn(Nt, V, generator=g, dtype=torch.float64)).to(dev)
+        chi = torch.complex(torch.randn(Nt, V, generator=g, dtype=torch.float64),
+                            torch.randn(Nt, V, generator=g, dtype=torch.float64)).to(dev)
+        timings = []
+        for team, inner, ns in candidates(params, num_sms, single_cta):
+            p = hmc.Params(**{**params.__dict__, "team_ctas": team, "inner_ctas": inner,
+                              "tile_slices": ns, "precision": hmc.PREC_MIXED})
+            ctx = hmc.Context(p)
+            ctx.cg_solve(phi, chi, tol=1e-30, max_iter=4, prec=hmc.PREC_MIXED,
+                         allow_not_converged=True)
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            stream = torch.cuda.current_stream()
+            s.record(stream)
+            for _ in range(reps):
+                ctx.cg_solve(phi, chi, tol=1e-30, max_iter=iters, prec=hmc.PREC_MIXED,
+                             allow_not_converged=True)
+            e.record(stream)
+            e.synchronize()
+            timings.append(((team, inner, ns), s.elapsed_time(e) * 1e-3 / (reps * iters)))
+            ctx.close()
+        team, inner, ns = pick(timings)
+        _cache[key] = (team, inner, ns)
+    return hmc.Params(**{**params.__dict__, "team_ctas": team, "inner_ctas": inner,
+                         "tile_slices": ns})

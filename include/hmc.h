@@ -85,6 +85,12 @@ typedef struct hmc_params {
                             (0: automatic) */
     int inner_ctas;      /* CTAs running the FP32 iterations of the mixed CG
                             (0: automatic; the FP64 steps use all CTAs) */
+    int operand_mode;    /* mixed path: 0 automatic, 1 stream E through shared
+                            memory on every application, 2 keep each CTA's rows
+                            of E resident for the whole solve (needs
+                            V <= 256 and one CTA per 128-site block; a chain
+                            with V <= 128 then keeps its FP32 CG vectors in
+                            shared memory too when they fit) */
 } hmc_params;
 
 typedef struct hmc_cg_stats {

@@ -4,7 +4,8 @@ For one chain it times short mixed CG solves with a fixed iteration count
 (max_iter iterations, convergence not required: the per-iteration cost does
 not depend on the residual) for candidate shapes -- CTAs of the persistent
 launch (team_ctas), CTAs of the FP32 inner loop (inner_ctas), time slices per
-tensor-core tile (tile_slices) -- and keeps the fastest.  Timing uses CUDA
+tensor-core tile (tile_slices), streamed or resident E (operand_mode) -- and
+keeps the fastest.  Timing uses CUDA
 events on the current stream around calls through the C ABI; results are
 cached per (L, Nt, team constraint) for the process.
 """
@@ -18,26 +19,32 @@ _cache = {}
 
 
 def candidates(params, num_sms, single_cta=False):
-    """Shapes worth timing for this lattice: one CTA, or teams sized to the
-    number of tensor-core tiles / FP64 tiles at each tile width."""
+    """Shapes (team_ctas, inner_ctas, tile_slices, operand_mode) worth timing:
+    streamed E with one CTA or teams sized to the tensor-core / FP64 tile
+    counts, and resident E (one CTA per 128-site block) where E fits."""
     V, Nt = params.V, params.Nt
     nti = (V + 127) // 128
+    vp = ((V + 63) // 64) * 64
     f64_tiles = ((V + 31) // 32) * ((Nt + 7) // 8)
     out = []
     for ns in (8, 16, 32):
         tiles = nti * ((Nt + ns - 1) // ns)
         if single_cta:
-            out.append((1, 1, ns))
+            out.append((1, 1, ns, 1))
+            if vp <= 256 and nti == 1 and ns <= 16:
+                out.append((1, 1, ns, 2))
             continue
         for inner in sorted({1, min(tiles, num_sms)}):
             for team in sorted({max(inner, min(f64_tiles, num_sms)), min(num_sms, max(inner, 1))}):
-                out.append((team, inner, ns))
+                out.append((team, inner, ns, 1))
+        if vp <= 256 and nti <= num_sms and ns <= 16:
+            out.append((max(nti, min(f64_tiles, num_sms)), nti, ns, 2))
     return sorted(set(out))
 
 
 def pick(timings):
     """(shape, seconds per iteration) pairs -> fastest shape (ties: fewer CTAs)."""
-    return min(timings, key=lambda kv: (kv[1], kv[0][0], kv[0][1], kv[0][2]))[0]
+    return min(timings, key=lambda kv: (kv[1],) + tuple(kv[0]))[0]
 
 
 def tune(params, iters=40, reps=2, single_cta=False, seed=1):
@@ -45,7 +52,7 @@ def tune(params, iters=40, reps=2, single_cta=False, seed=1):
     to the fastest measured shape."""
     key = (params.L, params.Nt, round(params.beta / params.Nt, 12), single_cta)
     if key in _cache:
-        team, inner, ns = _cache[key]
+        team, inner, ns, mode = _cache[key]
     else:
         dev = torch.device("cuda", torch.cuda.current_device())
         num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -55,9 +62,10 @@ def tune(params, iters=40, reps=2, single_cta=False, seed=1):
         chi = torch.complex(torch.randn(Nt, V, generator=g, dtype=torch.float64),
                             torch.randn(Nt, V, generator=g, dtype=torch.float64)).to(dev)
         timings = []
-        for team, inner, ns in candidates(params, num_sms, single_cta):
+        for team, inner, ns, mode in candidates(params, num_sms, single_cta):
             p = hmc.Params(**{**params.__dict__, "team_ctas": team, "inner_ctas": inner,
-                              "tile_slices": ns, "precision": hmc.PREC_MIXED})
+                              "tile_slices": ns, "operand_mode": mode,
+                              "precision": hmc.PREC_MIXED})
             ctx = hmc.Context(p)
             ctx.cg_solve(phi, chi, tol=1e-30, max_iter=4, prec=hmc.PREC_MIXED,
                          allow_not_converged=True)
@@ -69,9 +77,10 @@ def tune(params, iters=40, reps=2, single_cta=False, seed=1):
                              allow_not_converged=True)
             e.record(stream)
             e.synchronize()
-            timings.append(((team, inner, ns), s.elapsed_time(e) * 1e-3 / (reps * iters)))
+            timings.append(((team, inner, ns, mode),
+                            s.elapsed_time(e) * 1e-3 / (reps * iters)))
             ctx.close()
-        team, inner, ns = pick(timings)
-        _cache[key] = (team, inner, ns)
+        team, inner, ns, mode = pick(timings)
+        _cache[key] = (team, inner, ns, mode)
     return hmc.Params(**{**params.__dict__, "team_ctas": team, "inner_ctas": inner,
-                         "tile_slices": ns})
+                         "tile_slices": ns, "operand_mode": mode})

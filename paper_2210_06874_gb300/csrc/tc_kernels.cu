@@ -148,7 +148,13 @@ __device__ bool apply_team(const ChainView& c, const Team& tm, TcState& st,
                            const CUtensorMap* mhi, const CUtensorMap* mlo, int ns_tile,
                            const Src& src, float scale, float inv, Epi& epi) {
     const int nti = c.Vr / TM, ntt = (c.Nt + ns_tile - 1) / ns_tile;
-    for (int tile = tm.rank; tile < nti * ntt; tile += tm.size) {
+    // resident mode: the CTA's rows of E (site block = rank) stay in shared
+    // memory, so it takes all slice tiles of that block; streaming: tiles
+    // are dealt round robin
+    const bool res = st.mode == kResident;
+    const int first = tm.rank, step = res ? nti : tm.size;
+    const int last = res ? nti * ntt : nti * ntt;
+    for (int tile = first; tile < last; tile += step) {
         int i0, t0, ns;
         tile_coords(tile, nti, ns_tile, c.Nt, i0, t0, ns);
         if (!tc_tile<DAG>(st, mhi, mlo, c.V, c.Nt, c.Vp, i0, t0, ns, src, scale, inv, epi))
@@ -214,6 +220,8 @@ struct MixedResult {
 struct PersistentArgs {
     int ns_tile;
     int inner;         // CTAs of the FP32 inner loop
+    int mode;          // OperandMode: resident needs inner == number of site blocks
+    int vec_resident;  // resident mode with one CTA: FP32 CG vectors in shared memory
     double tol;
     int max_iter;
     double ru_delta;
@@ -275,21 +283,15 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
     Team ti = tm;
     ti.size = inner_size;
     ti.bar = c.bar + 2;
-    double v2[2] = {0.0, 0.0};
+    // FP64 solution and |chi|^2 on all CTAs
+    double v1[1] = {0.0};
     HMC_TEAM_ELEMS(e, c, tm) {
         const double2 ch = chi[e];
         x64[e] = make_double2(0.0, 0.0);
-        const float2 rv = make_float2((float)ch.x, (float)ch.y);
-        rf[e] = rv;
-        pf[e] = make_float2(0.f, 0.f);
-        xf[e] = make_float2(0.f, 0.f);
-        v2[0] += ch.x * ch.x + ch.y * ch.y;
-        v2[1] += (double)rv.x * rv.x + (double)rv.y * rv.y;
+        v1[0] += ch.x * ch.x + ch.y * ch.y;
     }
-    if (!team_sum<2>(tm, v2)) return false;
-    const double chi2 = v2[0];
-    double rr = v2[1], pp = rr, rmax = rr, rr_true = chi2, beta = 0.0;
-    bool refresh = false;
+    if (!team_sum<1>(tm, v1)) return false;
+    const double chi2 = v1[0];
     res.iterations = 0;
     res.reliable_updates = 0;
     res.status = HMC_OK;
@@ -298,6 +300,42 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
         if (!finite_d(chi2)) res.status = HMC_ERR_NONFINITE;
         return true;
     }
+    // FP32 iterates on the inner team (their owners).  A chain solved by one
+    // CTA with E resident keeps them in shared memory: r, p, p', q, x and the
+    // FP32 phase table, six vectors after the B ring.
+    double rr = 0.0;
+    const float2* cisf = c.cis_f;
+    if (in_inner) {
+        if (pa.mode == kResident) {
+            if (!tc_load_resident(st, mhi, mlo, tm.rank * TM, c.Vp / KCH)) return false;
+        } else {
+            tc_set_layout(st, kStreaming, 0);
+        }
+        if (pa.vec_resident) {
+            float2* sv = reinterpret_cast<float2*>(st.free_area());
+            rf = sv;
+            pf = sv + c.N;
+            pn = sv + 2 * c.N;
+            qf = sv + 3 * c.N;
+            xf = sv + 4 * c.N;
+            float2* cs = sv + 5 * c.N;
+            for (int e = threadIdx.x; e < c.N; e += blockDim.x) cs[e] = c.cis_f[e];
+            cisf = cs;
+        }
+        double v2[1] = {0.0};
+        HMC_TEAM_ELEMS(e, c, ti) {
+            const double2 ch = chi[e];
+            const float2 rv = make_float2((float)ch.x, (float)ch.y);
+            rf[e] = rv;
+            pf[e] = make_float2(0.f, 0.f);
+            xf[e] = make_float2(0.f, 0.f);
+            v2[0] += (double)rv.x * rv.x + (double)rv.y * rv.y;
+        }
+        if (!team_sum<1>(ti, v2)) return false;
+        rr = v2[0];
+    }
+    double pp = rr, rmax = rr, rr_true = chi2, beta = 0.0;
+    bool refresh = false;
     const double stop = pa.tol * pa.tol * chi2;
     const double ru2 = pa.ru_delta * pa.ru_delta;
     int it = 0;
@@ -311,7 +349,7 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
                 float sc, inv;
                 vector_scale(pp, sc, inv);
                 SrcDirection dir{rf, c.r, pf, (float)beta, refresh, c.V};
-                EpiDirection ed{dir, pn, rf, qf, c.cis_f, c.Nt, 0.f};
+                EpiDirection ed{dir, pn, rf, qf, cisf, c.Nt, 0.f};
                 if (!apply_team<true>(c, ti, st, mhi, mlo, pa.ns_tile, dir, sc, inv, ed))
                     return false;
                 double vq[1] = {(double)ed.acc};
@@ -325,7 +363,7 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
                 const double alpha = rr / qq;
                 // Ap = M q; x += alpha p; r -= alpha Ap
                 vector_scale(qq, sc, inv);
-                SrcPhase srcq{qf, c.cis_f, c.V};
+                SrcPhase srcq{qf, cisf, c.V};
                 EpiCgUpdate eu{qf, pf, xf, rf, (float)alpha, c.V, 0.f};
                 if (!apply_team<false>(c, ti, st, mhi, mlo, pa.ns_tile, srcq, sc, inv, eu))
                     return false;
@@ -339,6 +377,17 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
                 rr = rr_new;
                 pp = rr + beta * beta * pp;
             }
+            // fold the FP32 increment into x64 (the inner team owns x_f)
+            if (reason != kSegNonfinite) {
+                HMC_TEAM_ELEMS(e, c, ti) {
+                    const float2 d = xf[e];
+                    double2 xv = x64[e];
+                    xv.x += (double)d.x;
+                    xv.y += (double)d.y;
+                    x64[e] = xv;
+                    xf[e] = make_float2(0.f, 0.f);
+                }
+            }
             if (tm.rank == 0 && threadIdx.x == 0) {
                 seg[0] = reason;
                 seg[1] = it;
@@ -348,16 +397,7 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
         const int reason = (int)seg[0];
         it = (int)seg[1];
         if (reason == kSegNonfinite) { res.status = HMC_ERR_NONFINITE; break; }
-        // fold the FP32 increment into x64; FP64 true residual on all CTAs
-        HMC_TEAM_ELEMS(e, c, tm) {
-            const float2 d = xf[e];
-            double2 xv = x64[e];
-            xv.x += (double)d.x;
-            xv.y += (double)d.y;
-            x64[e] = xv;
-            xf[e] = make_float2(0.f, 0.f);
-        }
-        if (!team_barrier(tm)) return false;
+        // FP64 true residual on all CTAs
         if (!f64_residual(c, tm, sm64, chi, x64, rr_true)) return false;
         ++res.reliable_updates;
         if (!finite_d(rr_true)) { res.status = HMC_ERR_NONFINITE; break; }
@@ -729,10 +769,29 @@ static tc::PersistentArgs persistent_args(hmc_ctx* c, int grid, double tol, int 
     const ChainView& v = c->view;
     // inner team: one CTA while the whole lattice fits in a handful of tiles
     // (a single CTA needs no inter-CTA barrier), else the whole launch
-    pa.inner = (v.Vr / tc::TM) * ((v.Nt + 31) / 32) <= 2 ? 1 : grid;
-    if (c->params.inner_ctas > 0) pa.inner = std::min(c->params.inner_ctas, grid);
-    pa.ns_tile = pick_ns(v.Vr / tc::TM, v.Nt, pa.inner);
+    const int nti = v.Vr / tc::TM;
+    const int nk = v.Vp / tc::KCH;
+    // resident E when one site block's rows (all K) fit and every site block
+    // gets its own CTA; else stream E through the ring
+    const bool can_resident = nk <= tc::kMaxResidentChunks && nti <= grid;
+    pa.mode = (c->params.operand_mode == 2 || (c->params.operand_mode == 0 && can_resident))
+                  ? tc::kResident
+                  : tc::kStreaming;
+    if (pa.mode == tc::kResident && !can_resident) pa.mode = tc::kStreaming;
+    pa.vec_resident = 0;
+    if (pa.mode == tc::kResident) {
+        pa.inner = nti;
+        pa.ns_tile = std::min(16, pick_ns(1, v.Nt, 1));
+        const size_t free_bytes =
+            tc::kOperandBytes - (size_t)nk * tc::kAChunkBytes - tc::kMaxStages * tc::kBStageSmall;
+        pa.vec_resident = (nti == 1 && 6 * sizeof(float2) * (size_t)v.N <= free_bytes) ? 1 : 0;
+    } else {
+        pa.inner = nti * ((v.Nt + 31) / 32) <= 2 ? 1 : grid;
+        if (c->params.inner_ctas > 0) pa.inner = std::min(c->params.inner_ctas, grid);
+        pa.ns_tile = pick_ns(nti, v.Nt, pa.inner);
+    }
     if (c->params.tile_slices > 0) pa.ns_tile = c->params.tile_slices;
+    if (pa.mode == tc::kResident && pa.ns_tile > 16) pa.ns_tile = 16;   // 8 KB B stages
     pa.tol = tol;
     pa.max_iter = max_iter;
     pa.ru_delta = c->params.ru_delta;
@@ -852,8 +911,22 @@ int tc_batch_create(const hmc_params* p, int n, TcBatch** out) {
         it.v.E_hi = lv.E_hi;
         it.v.E_lo = lv.E_lo;
         it.pa.inner = 1;
-        it.pa.ns_tile = pick_ns(it.v.Vr / tc::TM, it.v.Nt, 1);
-        if (c->params.tile_slices > 0) it.pa.ns_tile = c->params.tile_slices;
+        {
+            // one CTA per chain: E resident when the chain has one site block
+            const int nti = it.v.Vr / tc::TM, nk = it.v.Vp / tc::KCH;
+            const bool res = nti == 1 && nk <= tc::kMaxResidentChunks &&
+                             c->params.operand_mode != 1;
+            it.pa.mode = res ? tc::kResident : tc::kStreaming;
+            it.pa.ns_tile = pick_ns(nti, it.v.Nt, 1);
+            if (c->params.tile_slices > 0) it.pa.ns_tile = c->params.tile_slices;
+            it.pa.vec_resident = 0;
+            if (res) {
+                it.pa.ns_tile = std::min(it.pa.ns_tile, 16);
+                const size_t free_bytes = tc::kOperandBytes - (size_t)nk * tc::kAChunkBytes -
+                                          tc::kMaxStages * tc::kBStageSmall;
+                it.pa.vec_resident = 6 * sizeof(float2) * (size_t)it.v.N <= free_bytes;
+            }
+        }
         it.pa.tol = c->params.cg_tol;
         it.pa.max_iter = c->params.cg_max_iter;
         it.pa.ru_delta = c->params.ru_delta;

@@ -14,8 +14,10 @@
 // B is built by six warps straight into the 128-byte-swizzled K-major
 // layout the MMA reads: for M the phase exp(i phi_{t-1}) is multiplied in;
 // for M^dag the source slice is t+1 and the conjugate phase of the target
-// slice is applied in the epilogue.  A ring of kStages operand stages with
-// full/empty mbarriers keeps TMA, B production and MMA issue overlapped.
+// slice is applied in the epilogue.  A ring of operand stages with full/empty
+// mbarriers keeps TMA, B production and MMA issue overlapped.  In resident
+// mode the CTA's rows of E_hi/E_lo (all K) stay in shared memory for a whole
+// solve and only B streams through the ring.
 #pragma once
 
 #include "tc_ptx.cuh"
@@ -27,12 +29,18 @@ constexpr int TM = 128;         // sites per tile (MMA M)
 constexpr int KCH = 64;         // K per chunk: one 128-byte swizzle row of fp16
 constexpr int NMAX = 64;        // max MMA N (= 2 * slices per tile)
 constexpr int NTHR = 256;       // threads per CTA (8 warps)
-constexpr int kStages = 4;      // depth of the operand ring
+constexpr int kMaxStages = 4;   // deepest operand ring
 constexpr uint32_t kTmemCols = 128;    // main accumulator at 0, correction at 64
 constexpr uint32_t kCorrCol = 64;
 constexpr float kLoScale = 2048.f;     // 2^11
 constexpr float kLoInv = 1.f / 2048.f;
-constexpr uint32_t kATileBytes = TM * 128;
+constexpr uint32_t kATileBytes = TM * 128;          // one 64-wide K chunk of E_hi (or E_lo)
+constexpr uint32_t kAChunkBytes = 2 * kATileBytes;  // E_hi + E_lo
+constexpr uint32_t kBTileBytes = NMAX * 128;        // one chunk of B_hi (or B_lo)
+constexpr uint32_t kBStageBytes = 2 * kBTileBytes;  // streaming B stage (N <= 64)
+constexpr uint32_t kBStageSmall = kBStageBytes / 2; // resident B stage (N <= 32)
+constexpr uint32_t kOperandBytes = 204 * 1024;      // operand area of dynamic smem
+constexpr int kMaxResidentChunks = 4;               // resident E: K <= 256
 // warp roles
 constexpr int kWarpTma = 0;            // lane 0 issues the TMA loads of E
 constexpr int kWarpMma = 1;            // lane 0 issues tcgen05.mma
@@ -40,24 +48,34 @@ constexpr int kFirstBWarp = 2;         // warps 2..7 build the B operand
 constexpr int kNumBWarps = 6;
 constexpr int kFirstEpiWarp = 4;       // warps 4..7 read TMEM (lane quarter = warp % 4)
 static_assert((NMAX / 2) * 8 <= 2 * kNumBWarps * 32, "build_B covers at most 2 items/thread");
+static_assert(kMaxStages * (kAChunkBytes + kBStageBytes) <= kOperandBytes, "streaming ring");
+static_assert(kMaxResidentChunks * kAChunkBytes + kMaxStages * kBStageSmall <= kOperandBytes,
+              "resident E + B ring");
 
-struct TileSmem {
-    uint8_t a_hi[kStages][TM * 128];
-    uint8_t a_lo[kStages][TM * 128];
-    uint8_t b_hi[kStages][NMAX * 128];
-    uint8_t b_lo[kStages][NMAX * 128];
-    uint64_t full[kStages];    // TMA bytes + one arrival per B warp
-    uint64_t empty[kStages];   // MMA commit: the stage may be refilled
-    uint64_t acc_full;         // MMA commit after a tile's last chunk
+// Barriers and the TMEM address follow the operand area.
+struct TileBars {
+    uint64_t full[kMaxStages];    // B producers (+ TMA bytes when streaming)
+    uint64_t empty[kMaxStages];   // MMA commit: the stage may be refilled
+    uint64_t acc_full;            // MMA commit after a tile's last chunk
+    uint64_t res_full;            // resident E landed
     uint32_t tmem_base;
 };
-constexpr size_t kSmemBytes = sizeof(TileSmem) + 1024;  // + alignment slack
+constexpr size_t kSmemBytes = kOperandBytes + sizeof(TileBars) + 1024;  // + alignment slack
 
-__device__ __forceinline__ TileSmem& tile_smem(uint8_t* dyn) {
+// Operand layouts of the dynamic shared memory (1024-byte aligned base);
+// four ring stages in both:
+//   streaming: stage s holds E_hi/E_lo chunk (32 KB) at s*32K and the B
+//              stage (16 KB, N <= 64) at 128K + s*16K; E streamed by TMA
+//   resident:  E_hi/E_lo of all nk K chunks of the CTA's site block at
+//              kc*32K (loaded once per solve), B stages (8 KB, N <= 32) at
+//              nk*32K + s*8K; the rest of the area can hold the FP32 CG
+//              vectors of a chain that one CTA solves alone
+enum OperandMode : int { kStreaming = 0, kResident = 1 };
+
+__device__ __forceinline__ uint8_t* smem_base(uint8_t* dyn) {
     const uint32_t a = smem_u32(dyn);
-    return *reinterpret_cast<TileSmem*>(dyn + ((1024u - (a & 1023u)) & 1023u));
+    return dyn + ((1024u - (a & 1023u)) & 1023u);
 }
-
 // Split 8 floats into fp16 hi and fp16 (x - hi) * 2^11, packed 8 per uint4.
 __device__ __forceinline__ void split8(const float (&x)[8], uint4& hi, uint4& lo) {
     uint32_t h[4], l[4];
@@ -214,29 +232,52 @@ __device__ __forceinline__ void build_B(const Src& src, int V, int Nt, int t0, i
 
 // Per-CTA state of the tensor-core tile pipeline (set up once per launch).
 struct TcState {
-    TileSmem* sm;
+    uint8_t* base;     // 1024-aligned operand area
+    TileBars* bars;
+    int mode;          // OperandMode
+    int stages;        // ring depth
+    uint32_t b_off;    // offset of the B ring
+    uint32_t b_stage;  // bytes per B stage (B_hi then B_lo, half each)
     uint32_t gchunk;   // chunks processed so far by this CTA (ring phases)
     uint32_t ntile;    // tiles processed so far (accumulator phases)
+    uint32_t nres;     // resident loads so far (phases of res_full)
     int* status;
+    __device__ __forceinline__ uint8_t* a_hi(int kc, int s) const {
+        return base + (mode == kResident ? kc : s) * kAChunkBytes;
+    }
+    __device__ __forceinline__ uint8_t* b_hi(int s) const {
+        return base + b_off + s * b_stage;
+    }
+    // first byte after the B ring (free for resident vectors)
+    __device__ __forceinline__ uint8_t* free_area() const {
+        return base + b_off + stages * b_stage;
+    }
 };
 
-// One-time set-up: mbarriers and TMEM.  All threads call it.
+// One-time set-up: mbarriers and TMEM, streaming layout.  All threads.
 __device__ inline void tc_setup(TcState& st, uint8_t* dyn, int* status) {
-    TileSmem& sm = tile_smem(dyn);
-    st.sm = &sm;
+    st.base = smem_base(dyn);
+    st.bars = reinterpret_cast<TileBars*>(st.base + kOperandBytes);
+    st.mode = kStreaming;
+    st.stages = kMaxStages;
+    st.b_off = kMaxStages * kAChunkBytes;
+    st.b_stage = kBStageBytes;
     st.gchunk = 0;
     st.ntile = 0;
+    st.nres = 0;
     st.status = status;
+    TileBars& b = *st.bars;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(smem_u32(&sm.full[s]), 1 + kNumBWarps);
-            mbar_init(smem_u32(&sm.empty[s]), 1);
+        for (int s = 0; s < kMaxStages; ++s) {
+            mbar_init(smem_u32(&b.full[s]), 1 + kNumBWarps);
+            mbar_init(smem_u32(&b.empty[s]), 1);
         }
-        mbar_init(smem_u32(&sm.acc_full), 1);
+        mbar_init(smem_u32(&b.acc_full), 1);
+        mbar_init(smem_u32(&b.res_full), 1);
         fence_mbar_init();
     }
     if ((threadIdx.x >> 5) == 0) {
-        tmem_alloc(smem_u32(&sm.tmem_base), kTmemCols);
+        tmem_alloc(smem_u32(&b.tmem_base), kTmemCols);
         tmem_relinquish();
     }
     fence_before_sync();
@@ -244,16 +285,52 @@ __device__ inline void tc_setup(TcState& st, uint8_t* dyn, int* status) {
     fence_after_sync();
 }
 
+// Choose the operand layout.  The ring depth is the same in both modes, so
+// the layout may change between solves or chains (no chunk is in flight
+// then: every tile waits for its accumulator before returning).
+__device__ inline void tc_set_layout(TcState& st, int mode, int nk) {
+    st.mode = mode;
+    if (mode == kResident) {
+        st.b_off = nk * kAChunkBytes;
+        st.b_stage = kBStageSmall;
+    } else {
+        st.b_off = kMaxStages * kAChunkBytes;
+        st.b_stage = kBStageBytes;
+    }
+}
+
+// Resident mode: load E_hi/E_lo rows i0..i0+127, all nk K chunks, into the
+// operand area with TMA and wait (bounded).  All threads call it, between
+// tiles.
+__device__ inline bool tc_load_resident(TcState& st, const CUtensorMap* mhi,
+                                        const CUtensorMap* mlo, int i0, int nk) {
+    TileBars& b = *st.bars;
+    tc_set_layout(st, kResident, nk);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t bar = smem_u32(&b.res_full);
+        mbar_arrive_expect_tx(bar, nk * kAChunkBytes);
+        for (int kc = 0; kc < nk; ++kc) {
+            tma_load_2d(smem_u32(st.a_hi(kc, 0)), mhi, kc * KCH, i0, bar);
+            tma_load_2d(smem_u32(st.a_hi(kc, 0) + kATileBytes), mlo, kc * KCH, i0, bar);
+        }
+    }
+    const bool ok = mbar_wait(smem_u32(&b.res_full), st.nres & 1, st.status);
+    st.nres += 1;
+    __syncthreads();
+    return ok;
+}
+
 // Tear-down: wait (bounded) for the last tile's MMAs, free TMEM.  All
 // threads call it.
 __device__ inline void tc_teardown(TcState& st) {
-    TileSmem& sm = *st.sm;
+    TileBars& b = *st.bars;
     if (st.ntile > 0 && *((volatile int*)st.status) != 0)
-        mbar_wait(smem_u32(&sm.acc_full), (st.ntile - 1) & 1, st.status);
+        mbar_wait(smem_u32(&b.acc_full), (st.ntile - 1) & 1, st.status);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-    if ((threadIdx.x >> 5) == 0) tmem_dealloc(sm.tmem_base, kTmemCols);
+    if ((threadIdx.x >> 5) == 0) tmem_dealloc(b.tmem_base, kTmemCols);
 }
 
 // Scale 2^e with |v| 2^e in [2^12, 2^13) for a vector of squared norm n2.
@@ -268,9 +345,10 @@ __device__ __forceinline__ void vector_scale(double n2, float& scale, float& inv
 }
 
 // One output tile: target slices t0 .. t0+ns-1 (ns <= NMAX/2), sites
-// i0 .. i0+127.  Warp-specialised: warp 0 streams E_hi/E_lo chunks with TMA,
-// warps 2..7 build the B chunks, warp 1 issues the MMAs as soon as a stage
-// is full and releases it with tcgen05.commit; kStages chunks are in flight.
+// i0 .. i0+127.  Warp-specialised: warp 0 streams E_hi/E_lo chunks with TMA
+// (streaming mode; in resident mode E is already in shared memory and warp 0
+// only signals), warps 2..7 build the B chunks, warp 1 issues the MMAs as
+// soon as a stage is full and releases it with tcgen05.commit.
 // The epilogue runs on warps 4..7: Epi::load(i, t) fetches what the output
 // (t, i) needs, Epi::store(i, t, in, w) receives w = (E u)_i for the tile's
 // source slice of target t (unscaled; before shift sign and phase).
@@ -279,36 +357,43 @@ template <bool DAG, class Src, class Epi>
 __device__ bool tc_tile(TcState& st, const CUtensorMap* mhi, const CUtensorMap* mlo, int V,
                         int Nt, int Vp, int i0, int t0, int ns, const Src& src, float scale,
                         float inv_scale, Epi& epi) {
-    TileSmem& sm = *st.sm;
+    TileBars& bars = *st.bars;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = Vp / KCH;
     const int N = ((2 * ns + 15) / 16) * 16;
+    const int S = st.stages;
+    const bool streaming = st.mode == kStreaming;
     const uint32_t g0 = st.gchunk;
     bool ok = true;
 
     if (warp == kWarpTma) {
         if (lane == 0) {
             for (int kc = 0; kc < nk && ok; ++kc) {
-                const uint32_t g = g0 + kc, s = g % kStages, n = g / kStages;
-                if (n > 0) ok = mbar_wait(smem_u32(&sm.empty[s]), (n - 1) & 1, st.status);
+                const uint32_t g = g0 + kc, s = g % S, n = g / S;
+                if (n > 0) ok = mbar_wait(smem_u32(&bars.empty[s]), (n - 1) & 1, st.status);
                 if (!ok) break;
-                const uint32_t bar = smem_u32(&sm.full[s]);
-                mbar_arrive_expect_tx(bar, 2 * kATileBytes);
-                tma_load_2d(smem_u32(sm.a_hi[s]), mhi, kc * KCH, i0, bar);
-                tma_load_2d(smem_u32(sm.a_lo[s]), mlo, kc * KCH, i0, bar);
+                const uint32_t bar = smem_u32(&bars.full[s]);
+                if (streaming) {
+                    mbar_arrive_expect_tx(bar, kAChunkBytes);
+                    tma_load_2d(smem_u32(st.a_hi(kc, s)), mhi, kc * KCH, i0, bar);
+                    tma_load_2d(smem_u32(st.a_hi(kc, s) + kATileBytes), mlo, kc * KCH, i0, bar);
+                } else {
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar)
+                                 : "memory");
+                }
             }
         }
     } else if (warp == kWarpMma) {
         if (lane == 0) {
             const uint32_t idesc = idesc_f16(TM, N);
-            const uint32_t tmem = sm.tmem_base;
+            const uint32_t tmem = bars.tmem_base;
             for (int kc = 0; kc < nk && ok; ++kc) {
-                const uint32_t g = g0 + kc, s = g % kStages, n = g / kStages;
-                ok = mbar_wait(smem_u32(&sm.full[s]), n & 1, st.status);
+                const uint32_t g = g0 + kc, s = g % S, n = g / S;
+                ok = mbar_wait(smem_u32(&bars.full[s]), n & 1, st.status);
                 if (!ok) break;
                 fence_after_sync();
-                const uint32_t ah = smem_u32(sm.a_hi[s]), al = smem_u32(sm.a_lo[s]);
-                const uint32_t bh = smem_u32(sm.b_hi[s]), bl = smem_u32(sm.b_lo[s]);
+                const uint32_t ah = smem_u32(st.a_hi(kc, s)), al = ah + kATileBytes;
+                const uint32_t bh = smem_u32(st.b_hi(s)), bl = bh + st.b_stage / 2;
 #pragma unroll
                 for (int kk = 0; kk < KCH / 16; ++kk) {
                     const uint32_t off = kk * 32;
@@ -319,23 +404,24 @@ __device__ bool tc_tile(TcState& st, const CUtensorMap* mhi, const CUtensorMap* 
                     mma_f16(tmem + kCorrCol, desc_sw128(al + off), desc_sw128(bh + off), idesc,
                             1u);
                 }
-                mma_commit(smem_u32(&sm.empty[s]));
+                mma_commit(smem_u32(&bars.empty[s]));
             }
-            mma_commit(smem_u32(&sm.acc_full));
+            mma_commit(smem_u32(&bars.acc_full));
         }
     } else {
         // B producers (warps 2..7)
         const int ptid = threadIdx.x - kFirstBWarp * 32, nprod = kNumBWarps * 32;
         for (int kc = 0; kc < nk && ok; ++kc) {
-            const uint32_t g = g0 + kc, s = g % kStages, n = g / kStages;
-            if (n > 0) ok = mbar_wait(smem_u32(&sm.empty[s]), (n - 1) & 1, st.status);
+            const uint32_t g = g0 + kc, s = g % S, n = g / S;
+            if (n > 0) ok = mbar_wait(smem_u32(&bars.empty[s]), (n - 1) & 1, st.status);
             if (!ok) break;
-            build_B<DAG>(src, V, Nt, t0, ns, N, kc * KCH, scale, sm.b_hi[s], sm.b_lo[s], ptid,
+            uint8_t* bh = st.b_hi(s);
+            build_B<DAG>(src, V, Nt, t0, ns, N, kc * KCH, scale, bh, bh + st.b_stage / 2, ptid,
                          nprod);
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
-                                            smem_u32(&sm.full[s]))
+                                            smem_u32(&bars.full[s]))
                                         : "memory");
         }
         // epilogue on warps 4..7: lane quarter (warp % 4) of TMEM, all columns.
@@ -354,11 +440,11 @@ __device__ bool tc_tile(TcState& st, const CUtensorMap* mhi, const CUtensorMap* 
                 }
             };
             if (ok) fetch(0, cur);
-            if (ok) ok = mbar_wait(smem_u32(&sm.acc_full), st.ntile & 1, st.status);
+            if (ok) ok = mbar_wait(smem_u32(&bars.acc_full), st.ntile & 1, st.status);
             fence_after_sync();
             ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld below is warp-collective
             if (ok) {
-                const uint32_t tl = sm.tmem_base + ((uint32_t)((warp & 3) * 32) << 16);
+                const uint32_t tl = bars.tmem_base + ((uint32_t)((warp & 3) * 32) << 16);
                 for (int cb = 0; cb < N; cb += 16) {
                     if (cb > 0) fetch(cb, cur);
                     float m[16], c[16];

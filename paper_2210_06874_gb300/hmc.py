@@ -47,7 +47,8 @@ class hmc_params(ctypes.Structure):
                 ("traj_length", ctypes.c_double), ("cg_tol", ctypes.c_double),
                 ("cg_max_iter", ctypes.c_int), ("precision", ctypes.c_int),
                 ("ru_delta", ctypes.c_double), ("team_ctas", ctypes.c_int),
-                ("tile_slices", ctypes.c_int), ("inner_ctas", ctypes.c_int)]
+                ("tile_slices", ctypes.c_int), ("inner_ctas", ctypes.c_int),
+                ("operand_mode", ctypes.c_int)]
 
 
 class hmc_cg_stats(ctypes.Structure):
@@ -141,6 +142,7 @@ class Params:
     team_ctas: int = 0
     tile_slices: int = 0
     inner_ctas: int = 0
+    operand_mode: int = 0
 
     @property
     def V(self):
@@ -154,7 +156,7 @@ class Params:
         return hmc_params(self.L, self.Nt, self.kappa, self.U, self.beta, self.n_md,
                           self.traj_length, self.cg_tol, self.cg_max_iter, self.precision,
                           self.ru_delta, self.team_ctas, self.tile_slices,
-                          self.inner_ctas)
+                          self.inner_ctas, self.operand_mode)
 
 
 class Context:

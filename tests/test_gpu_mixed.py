@@ -72,11 +72,12 @@ def test_apply_mixed_zero_vector():
     assert torch.count_nonzero(c.apply_M(phi, psi, prec=hmc.PREC_MIXED)) == 0
 
 
+@pytest.mark.parametrize("mode", [1, 2])       # streamed E / resident E
 @pytest.mark.parametrize("L,Nt,beta,U", [(1, 2, 1.0, 2.0), (3, 8, 2.0, 2.0), (6, 32, 4.0, 3.5),
-                                         (12, 64, 8.0, 3.8)])
-def test_cg_mixed_reaches_fp64_residual(L, Nt, beta, U):
+                                         (9, 16, 2.0, 3.0), (12, 64, 8.0, 3.8)])
+def test_cg_mixed_reaches_fp64_residual(L, Nt, beta, U, mode):
     V = 2 * L * L
-    c = hmc.Context(hmc.Params(L=L, Nt=Nt, beta=beta, U=U))
+    c = hmc.Context(hmc.Params(L=L, Nt=Nt, beta=beta, U=U, operand_mode=mode))
     E = oracle_E(L, Nt, beta)
     phi = synth.gaussian_field(11, Nt, V, beta / Nt * U, scale=0.5)
     chi = synth.complex_gaussian(12, Nt, V)
@@ -110,11 +111,12 @@ def test_force_from_mixed_solution(L, Nt):
     assert rel(F, Fo) < 1e-8
 
 
-def test_trajectory_mixed_matches_oracle():
+@pytest.mark.parametrize("mode", [1, 2])
+def test_trajectory_mixed_matches_oracle(mode):
     L, Nt, beta, U, n_md = 3, 8, 2.0, 2.0, 10
     delta = beta / Nt
     c = hmc.Context(hmc.Params(L=L, Nt=Nt, U=U, beta=beta, n_md=n_md, traj_length=1.0,
-                               cg_tol=1e-10, precision=hmc.PREC_MIXED))
+                               cg_tol=1e-10, precision=hmc.PREC_MIXED, operand_mode=mode))
     E = oracle_E(L, Nt, beta)
     phi_np = synth.gaussian_field(5, Nt, 18, delta * U, scale=0.5)
     phi = dev(phi_np)

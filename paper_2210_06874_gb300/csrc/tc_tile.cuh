@@ -48,6 +48,7 @@ constexpr int kFirstBWarp = 2;         // warps 2..7 build the B operand
 constexpr int kNumBWarps = 6;
 constexpr int kFirstEpiWarp = 4;       // warps 4..7 read TMEM (lane quarter = warp % 4)
 static_assert((NMAX / 2) * 8 <= 2 * kNumBWarps * 32, "build_B covers at most 2 items/thread");
+static_assert(kNumBWarps % 6 == 0, "producer groups of 1, 2 or 3");
 static_assert(kMaxStages * (kAChunkBytes + kBStageBytes) <= kOperandBytes, "streaming ring");
 static_assert(kMaxResidentChunks * kAChunkBytes + kMaxStages * kBStageSmall <= kOperandBytes,
               "resident E + B ring");
@@ -409,16 +410,30 @@ __device__ bool tc_tile(TcState& st, const CUtensorMap* mhi, const CUtensorMap* 
             mma_commit(smem_u32(&bars.acc_full));
         }
     } else {
-        // B producers (warps 2..7)
-        const int ptid = threadIdx.x - kFirstBWarp * 32, nprod = kNumBWarps * 32;
+        // B producers (warps 2..7).  A chunk has (N/2)*8 items; when one
+        // group of producer warps can hold a chunk at one item per thread,
+        // the six warps split into groups that build successive chunks at
+        // the same time (chunk kc goes to group kc % groups).  Every warp
+        // still waits for each chunk's stage and arrives on its full barrier
+        // (warps of other groups without writing), so the arrival count is
+        // the same for every chunk and no arrival can precede the stage's
+        // release.
+        const int pw = warp - kFirstBWarp;
+        const int items = (N >> 1) * 8;
+        const int groups = items <= 128 ? 3 : (items <= 192 ? 2 : 1);
+        const int gw = kNumBWarps / groups;              // warps per group
+        const int my_group = pw / gw;
+        const int ptid = (pw % gw) * 32 + lane, nprod = gw * 32;
         for (int kc = 0; kc < nk && ok; ++kc) {
             const uint32_t g = g0 + kc, s = g % S, n = g / S;
             if (n > 0) ok = mbar_wait(smem_u32(&bars.empty[s]), (n - 1) & 1, st.status);
             if (!ok) break;
-            uint8_t* bh = st.b_hi(s);
-            build_B<DAG>(src, V, Nt, t0, ns, N, kc * KCH, scale, bh, bh + st.b_stage / 2, ptid,
-                         nprod);
-            fence_proxy_async();
+            if (kc % groups == my_group) {
+                uint8_t* bh = st.b_hi(s);
+                build_B<DAG>(src, V, Nt, t0, ns, N, kc * KCH, scale, bh, bh + st.b_stage / 2,
+                             ptid, nprod);
+                fence_proxy_async();
+            }
             __syncwarp();
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
                                             smem_u32(&bars.full[s]))

@@ -145,3 +145,24 @@ def apply_M_brs(L, phi, psi, delta, kappa):
     ph = np.exp(1j * phi)
     diag_part = np.where(isA, fwd - ph * psi, psi - np.conj(ph) * bwd)
     return diag_part - delta * kappa * (psi @ h.T)
+
+
+def apply_Mdag_brs(L, phi, psi, delta, kappa):
+    """Adjoint of Eq. (2.2): (M^dag psi) = sum over rows of conj(M) psi.
+    A sites: the forward difference transposes to psi_{x,t-1} (wrap sign at
+    t = 0) and the diagonal to -e^{-i phi_{x,t}} psi_{x,t}; B sites: the
+    diagonal 1 and the sub-diagonal of row t+1 (phase of time t+1) give
+    psi_{x,t} - e^{+i phi_{x,t+1}} psi_{x,t+1} (wrap sign at t = Nt-1); the
+    real symmetric hopping is its own adjoint."""
+    Nt, V = phi.shape
+    sub = lattice.sublattice(L)
+    h = lattice.hopping_matrix(L)
+    isA = (sub == 0)[None, :]
+    bwd = np.roll(psi, 1, axis=0)              # psi_{t-1}
+    bwd[0] *= -1.0
+    fwd = np.roll(psi, -1, axis=0)             # psi_{t+1}
+    fwd[Nt - 1] *= -1.0
+    ph = np.exp(1j * phi)
+    ph_next = np.roll(ph, -1, axis=0)          # e^{i phi_{t+1}}
+    diag_part = np.where(isA, bwd - np.conj(ph) * psi, psi - ph_next * fwd)
+    return diag_part - delta * kappa * (psi @ h.T)

@@ -151,3 +151,27 @@ def test_brs_dense_vs_matrix_free(L, Nt):
     M = ops.dense_M_brs(L, phi, 0.25, 1.0)
     assert np.allclose(M @ psi.ravel(), ops.apply_M_brs(L, phi, psi, 0.25, 1.0).ravel(),
                        atol=1e-13)
+
+
+@pytest.mark.parametrize("L,Nt", [(1, 2), (2, 3), (3, 4)])
+def test_brs_adjoint_dense(L, Nt):
+    """The matrix-free adjoint of Eq. (2.2) is the conjugate transpose of the
+    dense matrix built from the equation."""
+    rng = np.random.default_rng(13)
+    V = 2 * L * L
+    phi = random_field(rng, Nt, V, 0.9)
+    psi = random_vec(rng, Nt, V)
+    M = ops.dense_M_brs(L, phi, 0.25, 1.0)
+    assert np.allclose(M.conj().T @ psi.ravel(),
+                       ops.apply_Mdag_brs(L, phi, psi, 0.25, 1.0).ravel(), atol=1e-13)
+
+
+def test_brs_adjoint_identity_large():
+    rng = np.random.default_rng(14)
+    L, Nt = 6, 16
+    V = 2 * L * L
+    phi = random_field(rng, Nt, V, 0.7)
+    u, v = random_vec(rng, Nt, V), random_vec(rng, Nt, V)
+    lhs = np.vdot(u, ops.apply_M_brs(L, phi, v, 0.125, 1.0))
+    rhs = np.vdot(ops.apply_Mdag_brs(L, phi, u, 0.125, 1.0), v)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)

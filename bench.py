@@ -38,8 +38,10 @@ def parse():
     ap.add_argument("--workload", default="l6_nt32")
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "mixed"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="trajectory", choices=["trajectory", "apply"],
+    ap.add_argument("--mode", default="trajectory", choices=["trajectory", "apply", "brs"],
                     help="trajectory: HMC trajectories/s; apply: M-applications/s")
+    ap.add_argument("--brs-L", type=int, default=102, help="brs mode: lattice size")
+    ap.add_argument("--brs-Nt", type=int, default=256, help="brs mode: time slices")
     ap.add_argument("--applies", type=int, default=20,
                     help="apply mode: applications of M per step")
     ap.add_argument("--chains", type=int, default=256, help="batch workload: chains")
@@ -150,6 +152,14 @@ def flops_per_apply(V, Nt):
     (~10 V Nt)."""
     return 4.0 * V * V * Nt + 10.0 * V * Nt
 
+
+
+def flush_l2(buf, acc):
+    """Evict the L2 between timed regions: a write larger than the L2, then a
+    read sweep of it, so the L2 holds clean lines and the timed work pays
+    no write-back of the flush's dirty lines."""
+    buf.fill_(1.0)
+    torch.sum(buf, dim=0, out=acc)
 
 def applies_per_traj(out, n_md):
     """M / M^dag applications in one trajectory: chi = M rho, two per CG
@@ -267,6 +277,7 @@ def run_ours(args):
         ctx.trajectory(phi, seed, traj, rank, allow_not_converged=True)
         traj += 1
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+    flush_acc = torch.empty((), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     clocks = ClockSampler(local_rank)
     if world > 1:
@@ -276,7 +287,7 @@ def run_ours(args):
     t_wall = time.perf_counter()
     total_ms, outs = 0.0, []
     for _ in range(args.steps):
-        flush.fill_(1.0)                       # evict L2 between timed trajectories
+        flush_l2(flush, flush_acc)          # evict L2 between timed trajectories
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record(stream)
         out = ctx.trajectory(phi, seed, traj, rank, allow_not_converged=True)
@@ -340,7 +351,7 @@ def run_ours(args):
         "config": {"workload": name, "precision": prec, "L": w["L"], "V": V, "Nt": Nt,
                    "U": w["U"], "beta": w["beta"], "n_md": params.n_md,
                    "cg_tol": params.cg_tol, "thermalisation_trajectories": n_therm,
-                   "l2": "flushed (256 MB write) between timed trajectories",
+                   "l2": "flushed (256 MB write + read sweep) between timed trajectories",
                    "parallelism": "replicas (one chain per GPU)",
                    "launch_shape": tuned or "automatic"},
         "m_applications_per_s": world * n_app / (ms_per_step * 1e-3),
@@ -396,12 +407,13 @@ def run_apply(args):
         ctx.apply_M(phi, psi, out, prec=p)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush_acc = torch.empty((), dtype=torch.float32, device=dev)
     clocks = ClockSampler(local_rank)
     torch.cuda.synchronize()
     clocks.start()
     total_ms = 0.0
     for _ in range(args.steps):
-        flush.fill_(1.0)
+        flush_l2(flush, flush_acc)
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record(stream)
         for _ in range(args.applies):
@@ -438,7 +450,7 @@ def run_apply(args):
             "data": "synthetic",
             "config": {"workload": name, "mode": "apply", "precision": prec, "V": V, "Nt": Nt,
                        "applies_per_step": args.applies,
-                       "l2": "flushed (256 MB write) between timed steps"},
+                       "l2": "flushed (256 MB write + read sweep) between timed steps"},
             "gpu_launches": n * 2 if prec != "fp64" else n * 2,
             "roofline": roof, "clocks": clk}
     if rank == 0:
@@ -549,8 +561,76 @@ def run_batch(args):
         print(json.dumps(line), flush=True)
 
 
+def run_brs(args):
+    """Eq. (2.2) operator (mixed differencing, sparse stencil) on the paper's
+    largest lattice, L = 102 (20,808 sites): M-applications/s against the HBM
+    roofline.  Algorithmic bytes per site-slice: input vector, phase table and
+    output once each (FP32: 24 B, FP64: 48 B)."""
+    import torch
+    from paper_2210_06874_gb300 import build_lib, hmc, synth
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    build_lib.build()
+    L, Nt, beta, kappa = args.brs_L, args.brs_Nt, 0.125 * args.brs_Nt, 1.0
+    V = 2 * L * L
+    N = V * Nt
+    dev = torch.device("cuda", local_rank)
+    prec = args.precision or "mixed"
+    phi = torch.from_numpy(synth.gaussian_field(7, Nt, V, 0.125 * 4.0, scale=0.5)).to(dev)
+    c64, c32 = hmc.brs_phases(L, Nt, phi)
+    dt = torch.complex128 if prec == "fp64" else torch.complex64
+    cis = c64 if prec == "fp64" else c32
+    psi = torch.from_numpy(synth.complex_gaussian(8, Nt, V)).to(dev).to(dt)
+    out = torch.empty_like(psi)
+    for _ in range(args.warmup):
+        hmc.apply_brs(L, Nt, beta / Nt * kappa, cis, psi, out)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush_acc = torch.empty((), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local_rank)
+    torch.cuda.synchronize()
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        for _ in range(args.applies):
+            flush_l2(flush, flush_acc)     # every application starts with a cold L2
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            hmc.apply_brs(L, Nt, beta / Nt * kappa, cis, psi, out)
+            e.record(stream)
+            e.synchronize()
+            times.append(s.elapsed_time(e))
+    clk = clocks.stop()
+    per_ms = statistics.median(times)
+    bpe = 48.0 if prec == "fp64" else 24.0
+    byts = bpe * N
+    peaks, kind = load_peaks()
+    hbm = peaks.get("hbm_gbs", FALLBACK["hbm_gbs"])
+    achieved = byts / (per_ms * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": 1e3 / per_ms, "unit": "M-applications/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
+            "data": "synthetic",
+            "config": {"workload": "brs_l%d_nt%d" % (L, Nt), "operator": "Eq. (2.2) stencil",
+                       "V": V, "Nt": Nt, "applies_per_step": args.applies,
+                       "l2": "flushed (256 MB write + read sweep) before every application; median"},
+            "gpu_launches": args.steps * args.applies,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None,
+                         "algorithmic_bytes_per_apply": byts,
+                         "peak_source": "%s STREAM-style copy" % kind},
+            "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.mode == "brs" and args.impl == "ours":
+        run_brs(args)
+        return
     if args.workload.startswith("batch") and args.impl == "ours":
         run_batch(args)
         return

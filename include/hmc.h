@@ -172,6 +172,27 @@ int hmc_action(hmc_ctx* ctx, const double* phi, const void* chi, const void* x, 
 int hmc_trajectory(hmc_ctx* ctx, double* phi, uint64_t seed, uint64_t traj_index,
                    uint32_t chain, hmc_traj_out* out, void* stream);
 
+/* ---- The printed operator, Eq. (2.2) -------------------------------------
+ * The mixed-differencing (Brower-Rebbi-Schaich) fermion operator exactly as
+ * Eq. (2.2) prints it, as a sparse stencil; no context needed.  With
+ * dk = delta*kappa and phi the phase angle (delta * phi_paper):
+ *   A site: (M psi)_{x,t} = psi_{x,t+1} - e^{+i phi_{x,t}} psi_{x,t} - dk sum_<y> psi_{y,t}
+ *   B site: (M psi)_{x,t} = psi_{x,t} - e^{-i phi_{x,t}} psi_{x,t-1} - dk sum_<y> psi_{y,t}
+ * antiperiodic in time; dagger = 1 applies the adjoint.  Layouts as above
+ * (time-major [Nt][V], site x = s*L*L + m1*L + m2). */
+
+/* Phase tables for hmc_apply_brs: cis64 (complex128, may be NULL) and cis32
+ * (complex64, may be NULL) = exp(i phi), device arrays of 2 L^2 Nt entries.
+ * Recompute whenever phi changes.  Asynchronous. */
+int hmc_brs_phases(int L, int Nt, const double* phi, void* cis64, void* cis32, void* stream);
+
+/* out = M in (dagger = 0) or M^dag in (dagger = 1) of Eq. (2.2).
+ * prec HMC_PREC_FP64: cis, in, out complex128; HMC_PREC_MIXED: complex64
+ * (FP32 arithmetic).  out must not alias in.  2 L^2 Nt < 2^31, Nt <= 65535.
+ * Asynchronous. */
+int hmc_apply_brs(int L, int Nt, double delta_kappa, const void* cis, const void* in, void* out,
+                  int prec, int dagger, void* stream);
+
 /* ---- Batched chains ----------------------------------------------------
  * Many independent Markov chains, each with its own hmc_params (lattice
  * size, Nt, U, beta, ...), advanced together: one persistent launch where

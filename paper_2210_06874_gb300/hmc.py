@@ -89,6 +89,9 @@ SIGNATURES = {
     "hmc_batch_layout": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.c_int]),
     "hmc_batch_trajectory": (ctypes.c_int, [_P, _P, ctypes.c_uint64, ctypes.c_uint64,
                                             ctypes.POINTER(hmc_traj_out), _P]),
+    "hmc_brs_phases": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
+    "hmc_apply_brs": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P,
+                                     ctypes.c_int, ctypes.c_int, _P]),
     "hmc_cg_solve_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P,
                                             ctypes.c_double, ctypes.c_int,
                                             ctypes.POINTER(hmc_cg_stats), _P]),
@@ -262,6 +265,36 @@ class Context:
                                                          chain, ctypes.byref(out), _stream()),
                allow)
         return out
+
+
+def brs_phases(L, Nt, phi):
+    """exp(i phi) tables (complex128, complex64) for apply_brs (Eq. (2.2))."""
+    lib = load_library()
+    V = 2 * L * L
+    if phi.dtype != torch.float64 or tuple(phi.shape) != (Nt, V) or not phi.is_contiguous():
+        raise ValueError("phi must be contiguous float64 [Nt, V]")
+    c64 = torch.empty((Nt, V), dtype=torch.complex128, device=phi.device)
+    c32 = torch.empty((Nt, V), dtype=torch.complex64, device=phi.device)
+    _check("hmc_brs_phases", lib.hmc_brs_phases(L, Nt, _ptr(phi), _ptr(c64), _ptr(c32),
+                                                _stream()))
+    return c64, c32
+
+
+def apply_brs(L, Nt, delta_kappa, cis, psi, out=None, dagger=False):
+    """M psi (or M^dag psi) of Eq. (2.2); complex128 -> FP64, complex64 -> FP32."""
+    lib = load_library()
+    V = 2 * L * L
+    prec = PREC_FP64 if psi.dtype == torch.complex128 else PREC_MIXED
+    for t in (cis, psi):
+        if t.dtype != psi.dtype or tuple(t.shape) != (Nt, V) or not t.is_contiguous():
+            raise ValueError("cis and psi must be contiguous [Nt, V] of the same complex dtype")
+    if out is None:
+        out = torch.empty_like(psi)
+    elif out.dtype != psi.dtype or tuple(out.shape) != (Nt, V) or not out.is_contiguous():
+        raise ValueError("out must be contiguous [Nt, V] of psi's dtype")
+    _check("hmc_apply_brs", lib.hmc_apply_brs(L, Nt, delta_kappa, _ptr(cis), _ptr(psi),
+                                              _ptr(out), prec, int(bool(dagger)), _stream()))
+    return out
 
 
 class Batch:

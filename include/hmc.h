@@ -91,6 +91,15 @@ typedef struct hmc_params {
                             V <= 256 and one CTA per 128-site block; a chain
                             with V <= 128 then keeps its FP32 CG vectors in
                             shared memory too when they fit) */
+    int cluster_mode;    /* mixed path, inner team of 2..8 CTAs: 0 automatic
+                            (launch it as one thread-block cluster, whose
+                            barriers and sums go through distributed shared
+                            memory, when the launch accepts the cluster; else
+                            global-memory barriers), 1 require the cluster
+                            (HMC_ERR_UNSUPPORTED if the launch refuses it),
+                            2 never.  Resident E accepts inner_ctas as a
+                            multiple of the 128-site blocks: the extra CTAs
+                            take further slice tiles of the same block. */
 } hmc_params;
 
 typedef struct hmc_cg_stats {

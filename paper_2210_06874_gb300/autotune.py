@@ -18,15 +18,40 @@ from . import hmc
 _cache = {}
 
 
+def small_feasible(V, Nt, C):
+    """Host copy of the feasibility rule of the CUDA-core cluster mode
+    (operand_mode 3): 1 <= C <= 8 CTAs, each with 1..16 time slices, and the
+    shared-memory layout within the 204 KB operand area."""
+    if C < 1 or C > 8 or Nt < C or -(-Nt // C) > 16:
+        return False
+    S = -(-Nt // C)
+    Vr = -(-V // 32) * 32
+    SP = 2 if S <= 2 else 4 if S <= 4 else 8 if S <= 8 else 16
+    G = Vr // 32
+    KS = min(1 if G >= 8 else 8 // G, V)
+    r16 = lambda b: (b + 15) // 16 * 16
+    total = (r16(V * Vr * 4) + 5 * r16(S * V * 8) + r16((S + 1) * V * 8) +
+             2 * r16(V * SP * 8) + 2 * r16(V * 8) + r16(KS * S * Vr * 8))
+    return total <= 204 * 1024
+
+
 def candidates(params, num_sms, single_cta=False):
     """Shapes (team_ctas, inner_ctas, tile_slices, operand_mode) worth timing:
     streamed E with one CTA or teams sized to the tensor-core / FP64 tile
-    counts, and resident E (one CTA per 128-site block) where E fits."""
+    counts, resident E (one CTA per 128-site block) where E fits, and the
+    CUDA-core cluster mode (clusters of 1, 2, 4 or 8 CTAs) where it fits."""
     V, Nt = params.V, params.Nt
     nti = (V + 127) // 128
     vp = ((V + 63) // 64) * 64
     f64_tiles = ((V + 31) // 32) * ((Nt + 7) // 8)
     out = []
+    for C in (1, 2, 4, 8):
+        if single_cta and C > 1:
+            break
+        if small_feasible(V, Nt, C):
+            teams = {C} if single_cta else {C, max(C, min(f64_tiles, num_sms) // C * C)}
+            for team in sorted(teams):
+                out.append((team, C, 8, 3))
     for ns in (8, 16, 32):
         tiles = nti * ((Nt + ns - 1) // ns)
         if single_cta:

@@ -89,13 +89,29 @@ constexpr int kVals = 4;
 constexpr int kSlots = 1;          // partial-sum buffers (one suffices, see team_sum)
 constexpr size_t kPartialDoubles = (size_t)kMaxTeam * kVals + kVals;
 
+// Synchronisation state of a team that is one thread-block cluster: every
+// CTA pushes its partial sums into every member's slot (distributed shared
+// memory) and arrives on every member's mbarrier; each CTA then waits on its
+// own mbarrier only.  Sync k uses barrier and slots k & 1: a member can only
+// start sync k+2 after every member has arrived for k+1, which each does
+// after finishing its wait (and reads) of sync k, so an early arrival for
+// the next sync never lands on the barrier a CTA is still waiting on, and a
+// slot is never rewritten while it may still be read.
+constexpr int kMaxCluster = 16;
+struct ClusterSync {
+    uint64_t bar[2];                       // one arrival per member per sync
+    unsigned count;                        // syncs this CTA has completed
+    double part[2][kMaxCluster][kVals];    // FP64 sums: [k & 1][member][value]
+    float part_f[2][kMaxCluster];          // FP32 sums: [k & 1][member]
+};
+
 struct Team {
     int rank;          // CTA rank within the team
     int size;          // number of CTAs in the team
     unsigned* bar;     // 2 words, zero-initialised
     int* status;       // shared device status word (hmc_status, 0 = ok)
     double* partials;  // kPartialDoubles
-    int slot;          // unused (kept for layout stability)
+    ClusterSync* cs;   // non-null: the team is this CTA's cluster, rank = cluster rank
 };
 
 __device__ __forceinline__ bool team_failed(const Team& tm) {
@@ -137,6 +153,111 @@ __device__ __forceinline__ void block_reduce(double (&v)[NV]) {
     }
 }
 
+__device__ __forceinline__ uint32_t cta_smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Hardware barrier over every thread of the cluster (all threads call it).
+__device__ __forceinline__ void cluster_barrier_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Set up the cluster team state; all threads of every member call it before
+// the first cluster sync.  Ends with a hardware cluster barrier, so no
+// member arrives remotely on a barrier that is not yet initialised.
+__device__ inline void cluster_sync_init(ClusterSync* cs, int size) {
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 2; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(cta_smem_u32(&cs->bar[b])),
+                         "r"(size)
+                         : "memory");
+        cs->count = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    cluster_barrier_all();
+}
+
+// Warp 0 of a cluster team, sync k = cs->count: lane r < size stores this
+// CTA's NV values (FP64 in `part`, or one FP32 in `part_f` when F32) into
+// member r's slot and arrives on member r's barrier k & 1 (release: orders
+// this CTA's earlier writes, shared and global, local and remote, before the
+// arrival).
+template <int NV, bool F32>
+__device__ inline void cluster_push(const Team& tm, const double* v, float vf) {
+    ClusterSync* cs = tm.cs;
+    const int par = (int)(cs->count & 1u);
+    const int lane = threadIdx.x & 31;
+    if (lane < tm.size) {
+        const uint32_t r = (uint32_t)lane;
+        uint32_t rs, rb;
+        if constexpr (F32) {
+            asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                         : "=r"(rs)
+                         : "r"(cta_smem_u32(&cs->part_f[par][tm.rank])), "r"(r));
+            asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(rs), "f"(vf) : "memory");
+        } else {
+            asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                         : "=r"(rs)
+                         : "r"(cta_smem_u32(&cs->part[par][tm.rank][0])), "r"(r));
+#pragma unroll
+            for (int j = 0; j < NV; ++j)
+                asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(rs + 8 * j), "d"(v[j])
+                             : "memory");
+        }
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                     : "=r"(rb)
+                     : "r"(cta_smem_u32(&cs->bar[par])), "r"(r));
+        asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(rb)
+                     : "memory");
+    }
+}
+
+// Lane 0 of a cluster team: wait (bounded, acquire) until every member has
+// arrived for sync cs->count.  False on timeout or team failure.  No global
+// memory is touched unless the wait runs long.
+__device__ inline bool cluster_wait(const Team& tm) {
+    ClusterSync* cs = tm.cs;
+    const unsigned k = cs->count;
+    const uint32_t bar = cta_smem_u32(&cs->bar[k & 1u]);
+    const uint32_t phase = (k >> 1) & 1u;
+    uint64_t t0 = 0;
+    for (unsigned n = 1;; ++n) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (done) return true;
+        if ((n & 1023u) == 0) {
+            if (t0 == 0) t0 = global_ns();
+            if (team_failed(tm)) return false;
+            if (global_ns() - t0 > kWaitLimitNs) {
+                set_status(tm.status, HMC_ERR_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+// Warp 0: push, then lane 0 waits.  Result valid on lane 0.
+template <int NV, bool F32>
+__device__ inline bool cluster_push_wait(const Team& tm, const double* v, float vf) {
+    cluster_push<NV, F32>(tm, v, vf);
+    if ((threadIdx.x & 31) != 0) return true;
+    return cluster_wait(tm);
+}
+
 // Team barrier fused with a deterministic sum of NV values (NV = 0: plain
 // barrier).  Every CTA writes its partials, then arrives on the counter; the
 // last CTA to arrive sums the partials of all ranks in rank order (a fixed
@@ -147,17 +268,52 @@ __device__ __forceinline__ void block_reduce(double (&v)[NV]) {
 // read every partial before it releases the barrier.
 // Returns false on every thread of the CTA if the team failed or a wait
 // timed out.
-template <int NV>
+// kPre: the CTA's values are already summed and valid on thread 0 only.
+// kF32: the values are FP32 numbers (held exactly in the doubles) and the
+// team sum is formed in FP32, in the order of the cluster path.
+template <int NV, bool kPre = false, bool kF32 = false>
 __device__ inline bool team_sync(Team& tm, double* v) {
     __shared__ int s_ok;
     __shared__ int s_last;
     __shared__ double s_out[NV > 0 ? NV : 1];
-    if constexpr (NV > 0) block_reduce<NV>(*reinterpret_cast<double(*)[NV]>(v));
+    if constexpr (NV > 0 && !kPre) block_reduce<NV>(*reinterpret_cast<double(*)[NV]>(v));
     if (tm.size == 1) {
         if (threadIdx.x == 0) {
 #pragma unroll
             for (int j = 0; j < NV; ++j) s_out[j] = v[j];
-            s_ok = !team_failed(tm);
+            s_ok = 1;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] = s_out[j];
+        const int ok = s_ok;
+        __syncthreads();
+        return ok != 0;
+    }
+    if (tm.cs) {
+        // cluster team: same summation order as the global path below
+        // (lane r holds member r's partial, then a fixed shuffle tree)
+        if (threadIdx.x < 32) {
+            double pv[NV > 0 ? NV : 1];
+#pragma unroll
+            for (int j = 0; j < NV; ++j) pv[j] = __shfl_sync(0xffffffffu, v[j], 0);
+            const bool ok = cluster_push_wait<NV, false>(tm, pv, 0.f);
+            if (threadIdx.x == 0) {
+                s_last = (int)(tm.cs->count & 1u);
+                tm.cs->count += 1u;
+                s_ok = ok ? 1 : 0;
+            }
+        }
+        __syncthreads();
+        if (NV > 0 && threadIdx.x < 32) {
+            const int par = s_last, lane = threadIdx.x;
+#pragma unroll
+            for (int j = 0; j < NV; ++j) {
+                double a = lane < tm.size ? tm.cs->part[par][lane][j] : 0.0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+                if (lane == 0) s_out[j] = a;
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -185,14 +341,26 @@ __device__ inline bool team_sync(Team& tm, double* v) {
             const int lane = threadIdx.x;
 #pragma unroll
             for (int j = 0; j < NV; ++j) {
-                double a = 0.0;
-                for (int r = lane; r < tm.size; r += 32)
-                    a += ((volatile double*)tm.partials)[r * kVals + j];
+                if constexpr (kF32) {
+                    float a = 0.f;
+                    for (int r = lane; r < tm.size; r += 32)
+                        a += (float)((volatile double*)tm.partials)[r * kVals + j];
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-                if (lane == 0) {
-                    totals[j] = a;
-                    s_out[j] = a;
+                    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+                    if (lane == 0) {
+                        totals[j] = (double)a;
+                        s_out[j] = (double)a;
+                    }
+                } else {
+                    double a = 0.0;
+                    for (int r = lane; r < tm.size; r += 32)
+                        a += ((volatile double*)tm.partials)[r * kVals + j];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+                    if (lane == 0) {
+                        totals[j] = a;
+                        s_out[j] = a;
+                    }
                 }
             }
         }
@@ -234,6 +402,125 @@ __device__ inline bool team_barrier(Team& tm) { return team_sync<0>(tm, nullptr)
 template <int NV>
 __device__ inline bool team_sum(Team& tm, double (&v)[NV]) {
     return team_sync<NV>(tm, v);
+}
+
+// Team sum of one FP32 value per thread, in FP32 throughout (the inner CG
+// loop's norms): warps reduce with a fixed shuffle tree, thread 0 adds the
+// warp sums in warp order, members' sums are added in rank order.  No FP64
+// arithmetic (slow on this part) and, for a one-CTA or cluster team, no
+// global memory.  Result on every thread.
+__device__ inline bool team_sum_f(Team& tm, float x, float& out) {
+    __shared__ float s_w[32];
+    __shared__ float s_tot;
+    __shared__ int s_fok;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) s_w[warp] = x;
+    __syncthreads();
+    if (tm.size > 1 && !tm.cs) {
+        // global-memory team: the CTAs' FP32 sums, added in FP32 in the
+        // order of the cluster path (same bits for the same team)
+        double v[1] = {0.0};
+        if (threadIdx.x == 0) {
+            float a = 0.f;
+            for (int w = 0; w < nw; ++w) a += s_w[w];
+            v[0] = (double)a;
+        }
+        const bool ok = team_sync<1, true, true>(tm, v);
+        out = (float)v[0];
+        return ok;
+    }
+    if (warp == 0) {
+        float a = 0.f;
+        if (lane == 0)
+            for (int w = 0; w < nw; ++w) a += s_w[w];
+        a = __shfl_sync(0xffffffffu, a, 0);
+        if (tm.size == 1) {
+            if (lane == 0) {
+                s_tot = a;
+                s_fok = 1;
+            }
+        } else {
+            const bool ok = cluster_push_wait<1, true>(tm, nullptr, a);
+            const int par = (int)(tm.cs->count & 1u);
+            __syncwarp();
+            float b = lane < tm.size ? tm.cs->part_f[par][lane] : 0.f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) b += __shfl_down_sync(0xffffffffu, b, o);
+            if (lane == 0) {
+                s_tot = b;
+                s_fok = ok ? 1 : 0;
+                tm.cs->count += 1u;
+            }
+        }
+    }
+    __syncthreads();
+    out = s_tot;
+    const bool ok = s_fok != 0;
+    __syncthreads();
+    return ok;
+}
+
+// Split-phase FP32 team sum for a one-CTA or cluster team (the small-lattice
+// CG overlaps its contractions with the cluster sums).  sum_begin: all
+// threads pass their values; the CTA's FP32 sum (fixed order) is pushed to
+// every member.  sum_end: all threads; waits for the members and returns
+// the total, summed in FP32 in rank order, on every thread.  Nothing but
+// __syncthreads-separated work may use the team between the two.
+struct SplitSum {
+    float w[32];
+    float single;
+    float tot;
+    int ok;
+};
+
+__device__ inline void sum_begin(const Team& tm, SplitSum& ss, float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) ss.w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        float a = 0.f;
+        if (lane == 0)
+            for (int w = 0; w < nw; ++w) a += ss.w[w];
+        a = __shfl_sync(0xffffffffu, a, 0);
+        if (tm.size == 1) {
+            if (lane == 0) ss.single = a;
+        } else {
+            cluster_push<1, true>(tm, nullptr, a);
+        }
+    }
+}
+
+__device__ inline bool sum_end(const Team& tm, SplitSum& ss, float& out) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        if (tm.size == 1) {
+            if (lane == 0) {
+                ss.tot = ss.single;
+                ss.ok = 1;
+            }
+        } else {
+            bool ok = true;
+            if (lane == 0) ok = cluster_wait(tm);
+            __syncwarp();
+            const int par = (int)(tm.cs->count & 1u);
+            float b = lane < tm.size ? tm.cs->part_f[par][lane] : 0.f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) b += __shfl_down_sync(0xffffffffu, b, o);
+            __syncwarp();
+            if (lane == 0) {
+                ss.tot = b;
+                ss.ok = ok ? 1 : 0;
+                tm.cs->count += 1u;
+            }
+        }
+    }
+    __syncthreads();
+    out = ss.tot;
+    return ss.ok != 0;
 }
 
 __device__ __forceinline__ bool finite_d(double a) { return isfinite(a); }

@@ -43,7 +43,7 @@ __device__ __forceinline__ Team make_team(const ChainView& c) {
     tm.bar = c.bar;
     tm.status = c.status;
     tm.partials = c.partials;
-    tm.slot = 0;
+    tm.cs = nullptr;
     return tm;
 }
 

@@ -13,6 +13,7 @@
 #include "fp64_path.cuh"
 #include "tc_path.h"
 #include "tc_tile.cuh"
+#include "small_cg.cuh"
 
 namespace hmc {
 
@@ -148,13 +149,10 @@ __device__ bool apply_team(const ChainView& c, const Team& tm, TcState& st,
                            const CUtensorMap* mhi, const CUtensorMap* mlo, int ns_tile,
                            const Src& src, float scale, float inv, Epi& epi) {
     const int nti = c.Vr / TM, ntt = (c.Nt + ns_tile - 1) / ns_tile;
-    // resident mode: the CTA's rows of E (site block = rank) stay in shared
-    // memory, so it takes all slice tiles of that block; streaming: tiles
-    // are dealt round robin
-    const bool res = st.mode == kResident;
-    const int first = tm.rank, step = res ? nti : tm.size;
-    const int last = res ? nti * ntt : nti * ntt;
-    for (int tile = first; tile < last; tile += step) {
+    // tiles are dealt round robin over the team; in resident mode the team
+    // size is a multiple of the site blocks, so a CTA only meets tiles of
+    // its own site block (rank mod nti), whose rows of E it holds
+    for (int tile = tm.rank; tile < nti * ntt; tile += tm.size) {
         int i0, t0, ns;
         tile_coords(tile, nti, ns_tile, c.Nt, i0, t0, ns);
         if (!tc_tile<DAG>(st, mhi, mlo, c.V, c.Nt, c.Vp, i0, t0, ns, src, scale, inv, epi))
@@ -220,7 +218,8 @@ struct MixedResult {
 struct PersistentArgs {
     int ns_tile;
     int inner;         // CTAs of the FP32 inner loop
-    int mode;          // OperandMode: resident needs inner == number of site blocks
+    int cluster;       // > 1: launched in clusters of this size, the inner team is cluster 0
+    int mode;          // OperandMode: resident needs inner a multiple of the site blocks
     int vec_resident;  // resident mode with one CTA: FP32 CG vectors in shared memory
     double tol;
     int max_iter;
@@ -273,16 +272,61 @@ __device__ bool f64_residual(const ChainView& c, Team& tm, f64::Smem& sm, const 
 // x / r update inside the M one.  Needs c.cis and c.cis_f of the current phi.
 enum SegmentEnd : int { kSegUpdate = 1, kSegMaxIter = 2, kSegNonfinite = 3 };
 
+// Scalar state of the FP32 iteration, kept and updated by thread 0 alone
+// and read by the other threads after a barrier, in FP32 (the iterates are
+// FP32; FP64 arithmetic runs at a small fraction of the FP32 rate and with
+// long latency on this part).  rr = |r|^2, pp = |p|^2 estimate (sets the
+// vector scale of the tensor-core operands), rmax = |r|^2 at the last
+// reliable update; stop and ru2 are the FP32 images of the FP64 criteria.
+struct CgScalars {
+    float rr, pp, rmax, alpha, beta, sc, inv, stop, ru2;
+    int it, reason;
+};
+
+// Thread 0, after qq = |q|^2: alpha and the scale of q.
+__device__ __forceinline__ void cg_after_q(CgScalars& s, float qq) {
+    int rs = 0;
+    if (!isfinite(qq) || !(qq > 0.f)) {
+        rs = kSegNonfinite;
+    } else {
+        s.alpha = s.rr / qq;
+        vector_scale_f(qq, s.sc, s.inv);
+    }
+    s.reason = rs;
+}
+
+// Thread 0, after rr_new = |r|^2: segment end, or beta, pp and the scale of
+// the next direction.
+__device__ __forceinline__ void cg_after_r(CgScalars& s, float rr_new) {
+    int rs = 0;
+    s.it += 1;
+    if (!isfinite(rr_new)) {
+        rs = kSegNonfinite;
+    } else if (rr_new <= s.stop || rr_new <= s.ru2 * s.rmax) {
+        rs = kSegUpdate;
+    } else {
+        const float b = rr_new / s.rr;
+        s.beta = b;
+        s.rr = rr_new;
+        s.pp = fmaf(b * b, s.pp, rr_new);
+        vector_scale_f(s.pp, s.sc, s.inv);
+    }
+    s.reason = rs;
+}
+
+template <bool SMALL>
 __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& sm64,
                          const CUtensorMap* mhi, const CUtensorMap* mlo,
-                         const PersistentArgs& pa, const double2* chi, double2* x64,
-                         MixedResult& res) {
+                         const PersistentArgs& pa, ClusterSync* ics, const double2* chi,
+                         double2* x64, MixedResult& res) {
     float2 *rf = c.r_f, *pf = c.p_f, *pn = c.p2_f, *qf = c.q_f, *xf = c.x_f;
     const int inner_size = min(max(pa.inner, 1), tm.size);
     const bool in_inner = tm.rank < inner_size;
     Team ti = tm;
     ti.size = inner_size;
     ti.bar = c.bar + 2;
+    // inner team = cluster 0: its barriers stay inside the cluster
+    ti.cs = (ics && pa.cluster > 1 && inner_size == pa.cluster) ? ics : nullptr;
     // FP64 solution and |chi|^2 on all CTAs
     double v1[1] = {0.0};
     HMC_TEAM_ELEMS(e, c, tm) {
@@ -305,9 +349,19 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
     // FP32 phase table, six vectors after the B ring.
     double rr = 0.0;
     const float2* cisf = c.cis_f;
-    if (in_inner) {
+    SmallCg sm;
+    if constexpr (SMALL) {
+      if (in_inner) {
+        // small lattice: FP32 iterates of the cluster's slices in shared memory
+        small_init_view(sm, st.base, tm.rank, inner_size, c.V, c.Nt);
+        double v2[1] = {small_setup(sm, c, chi)};
+        if (!team_sum<1>(ti, v2)) return false;
+        rr = v2[0];
+      }
+    } else if (in_inner) {
         if (pa.mode == kResident) {
-            if (!tc_load_resident(st, mhi, mlo, tm.rank * TM, c.Vp / KCH)) return false;
+            if (!tc_load_resident(st, mhi, mlo, (tm.rank % (c.Vr / TM)) * TM, c.Vp / KCH))
+                return false;
         } else {
             tc_set_layout(st, kStreaming, 0);
         }
@@ -334,48 +388,98 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
         if (!team_sum<1>(ti, v2)) return false;
         rr = v2[0];
     }
-    double pp = rr, rmax = rr, rr_true = chi2, beta = 0.0;
+    __shared__ CgScalars s_cg;
+    double rr_true = chi2;
     bool refresh = false;
     const double stop = pa.tol * pa.tol * chi2;
-    const double ru2 = pa.ru_delta * pa.ru_delta;
-    int it = 0;
+    if (threadIdx.x == 0) {
+        s_cg.rr = (float)rr;
+        s_cg.pp = (float)rr;
+        s_cg.rmax = (float)rr;
+        s_cg.beta = 0.f;
+        s_cg.stop = (float)stop;
+        s_cg.ru2 = (float)(pa.ru_delta * pa.ru_delta);
+        s_cg.it = 0;
+        vector_scale(rr, s_cg.sc, s_cg.inv);
+    }
+    __syncthreads();
     bool conv = false;
     volatile double* seg = c.scalars + 12;   // [0] end reason, [1] iterations
     for (;;) {
-        if (in_inner) {
+        if (SMALL && in_inner) {
+            // small lattice: contractions overlapped with the cluster sums
+            __shared__ SplitSum s_ss;
+            int reason = 0;
+            if (refresh) {
+                small_refresh_r(sm, c.r);
+                refresh = false;
+            }
+            __syncthreads();
+            small_prime(sm);
+            if (!team_barrier(ti)) return false;   // halos pushed, operands written
+            small_matvec_any(sm, sm.v(sm.l.ud));
+            __syncthreads();
+            small_matvec_col(sm, sm.v(sm.l.hr), sm.S - 1);
+            __syncthreads();
+            if (s_cg.it >= pa.max_iter) reason = kSegMaxIter;
+            while (reason == 0) {
+                // q = M^dag p' (p' = r + beta p); E (e^{i phi} q) overlaps |q|^2
+                float qq, rr_new;
+                sum_begin(ti, s_ss, small_dag_epilogue(sm, s_cg.beta));
+                small_matvec_any(sm, sm.v(sm.l.um));
+                if (!sum_end(ti, s_ss, qq)) return false;
+                if (threadIdx.x == 0) cg_after_q(s_cg, qq);
+                __syncthreads();
+                if (s_cg.reason != 0) { reason = s_cg.reason; break; }
+                small_matvec_col(sm, sm.v(sm.l.hq), 0);
+                __syncthreads();
+                // x += alpha p', r -= alpha M q; E r overlaps |r|^2
+                sum_begin(ti, s_ss, small_m_epilogue(sm, s_cg.alpha));
+                small_matvec_any(sm, sm.v(sm.l.ud));
+                if (!sum_end(ti, s_ss, rr_new)) return false;
+                if (threadIdx.x == 0) {
+                    cg_after_r(s_cg, rr_new);
+                    if (s_cg.reason == 0 && s_cg.it >= pa.max_iter) s_cg.reason = kSegMaxIter;
+                }
+                __syncthreads();
+                if (s_cg.reason != 0) { reason = s_cg.reason; break; }
+                small_matvec_col(sm, sm.v(sm.l.hr), sm.S - 1);
+                __syncthreads();
+            }
+            if (reason != kSegNonfinite) small_fold_x(sm, x64);
+            if (tm.rank == 0 && threadIdx.x == 0) {
+                seg[0] = reason;
+                seg[1] = s_cg.it;
+            }
+        } else if (!SMALL && in_inner) {
             int reason = kSegMaxIter;
-            while (it < pa.max_iter) {
+            while (s_cg.it < pa.max_iter) {
                 // p_new = r + beta p; q = M^dag p_new
-                float sc, inv;
-                vector_scale(pp, sc, inv);
-                SrcDirection dir{rf, c.r, pf, (float)beta, refresh, c.V};
+                SrcDirection dir{rf, c.r, pf, s_cg.beta, refresh, c.V};
                 EpiDirection ed{dir, pn, rf, qf, cisf, c.Nt, 0.f};
-                if (!apply_team<true>(c, ti, st, mhi, mlo, pa.ns_tile, dir, sc, inv, ed))
+                if (!apply_team<true>(c, ti, st, mhi, mlo, pa.ns_tile, dir, s_cg.sc, s_cg.inv,
+                                      ed))
                     return false;
-                double vq[1] = {(double)ed.acc};
-                if (!team_sum<1>(ti, vq)) return false;
+                float qq;
+                if (!team_sum_f(ti, ed.acc, qq)) return false;
                 float2* t = pf;
                 pf = pn;
                 pn = t;
                 refresh = false;
-                const double qq = vq[0];
-                if (!finite_d(qq) || !(qq > 0.0)) { reason = kSegNonfinite; break; }
-                const double alpha = rr / qq;
+                if (threadIdx.x == 0) cg_after_q(s_cg, qq);
+                __syncthreads();
+                if (s_cg.reason != 0) { reason = s_cg.reason; break; }
                 // Ap = M q; x += alpha p; r -= alpha Ap
-                vector_scale(qq, sc, inv);
                 SrcPhase srcq{qf, cisf, c.V};
-                EpiCgUpdate eu{qf, pf, xf, rf, (float)alpha, c.V, 0.f};
-                if (!apply_team<false>(c, ti, st, mhi, mlo, pa.ns_tile, srcq, sc, inv, eu))
+                EpiCgUpdate eu{qf, pf, xf, rf, s_cg.alpha, c.V, 0.f};
+                if (!apply_team<false>(c, ti, st, mhi, mlo, pa.ns_tile, srcq, s_cg.sc, s_cg.inv,
+                                       eu))
                     return false;
-                double vr[1] = {(double)eu.acc};
-                if (!team_sum<1>(ti, vr)) return false;
-                const double rr_new = vr[0];
-                ++it;
-                if (!finite_d(rr_new)) { reason = kSegNonfinite; break; }
-                if (rr_new <= stop || rr_new <= ru2 * rmax) { reason = kSegUpdate; break; }
-                beta = rr_new / rr;
-                rr = rr_new;
-                pp = rr + beta * beta * pp;
+                float rr_new;
+                if (!team_sum_f(ti, eu.acc, rr_new)) return false;
+                if (threadIdx.x == 0) cg_after_r(s_cg, rr_new);
+                __syncthreads();
+                if (s_cg.reason != 0) { reason = s_cg.reason; break; }
             }
             // fold the FP32 increment into x64 (the inner team owns x_f)
             if (reason != kSegNonfinite) {
@@ -390,12 +494,12 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
             }
             if (tm.rank == 0 && threadIdx.x == 0) {
                 seg[0] = reason;
-                seg[1] = it;
+                seg[1] = s_cg.it;
             }
         }
         if (!team_barrier(tm)) return false;
         const int reason = (int)seg[0];
-        it = (int)seg[1];
+        const int it = (int)seg[1];
         if (reason == kSegNonfinite) { res.status = HMC_ERR_NONFINITE; break; }
         // FP64 true residual on all CTAs
         if (!f64_residual(c, tm, sm64, chi, x64, rr_true)) return false;
@@ -404,17 +508,33 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
         if (rr_true <= stop) { conv = true; break; }
         if (reason == kSegMaxIter) break;
         // continue from the true residual; keep the direction
-        beta = rr_true / rr;
-        rr = rr_true;
-        rmax = rr_true;
-        pp = rr + beta * beta * pp;
+        if (threadIdx.x == 0) {
+            const double b = rr_true / (double)s_cg.rr;
+            const double pp = rr_true + b * b * (double)s_cg.pp;
+            s_cg.beta = (float)b;
+            s_cg.rr = (float)rr_true;
+            s_cg.rmax = (float)rr_true;
+            s_cg.pp = (float)pp;
+            s_cg.it = it;
+            vector_scale(pp, s_cg.sc, s_cg.inv);
+        }
+        __syncthreads();
         refresh = true;
     }
-    res.iterations = it;
+    res.iterations = (int)seg[1];
     if (!conv && res.status == HMC_OK) res.status = HMC_ERR_CG_NOT_CONVERGED;
     res.true_res = sqrt(rr_true / chi2);
     if (!finite_d(res.true_res)) res.status = HMC_ERR_NONFINITE;
     return true;
+}
+
+// Cluster launch: set up the cluster team state and check that the inner
+// team's ranks are the cluster ranks of cluster 0.
+__device__ inline void cluster_begin(const PersistentArgs& pa, ClusterSync* cs, int* status) {
+    if (pa.cluster <= 1) return;
+    if (threadIdx.x == 0 && cluster_ctarank() != (uint32_t)(blockIdx.x % pa.cluster))
+        set_status(status, HMC_ERR_UNSUPPORTED);
+    cluster_sync_init(cs, pa.cluster);
 }
 
 __device__ __forceinline__ Team make_team(const ChainView& c) {
@@ -424,7 +544,7 @@ __device__ __forceinline__ Team make_team(const ChainView& c) {
     tm.bar = c.bar;
     tm.status = c.status;
     tm.partials = c.partials;
-    tm.slot = 0;
+    tm.cs = nullptr;
     return tm;
 }
 
@@ -438,33 +558,56 @@ __device__ __forceinline__ void set_phases(const ChainView& c, const Team& tm,
     }
 }
 
+// Per-launch set-up of the operand area: the tensor-core path takes its
+// mbarriers and TMEM; the small (CUDA-core) mode needs only the area.
+template <bool SMALL>
+__device__ inline void persistent_setup(TcState& st, uint8_t* dyn, int* status) {
+    if constexpr (SMALL) {
+        st.base = smem_base(dyn);
+        st.status = status;
+        st.ntile = 0;
+    } else {
+        tc_setup(st, dyn, status);
+    }
+}
+template <bool SMALL>
+__device__ inline void persistent_teardown(TcState& st) {
+    if constexpr (!SMALL) tc_teardown(st);
+}
+
 // scalars: [0] iterations [1] true residual [2] status [3] reliable updates
+// SMALL: the FP32 iterations run in the CUDA-core cluster mode.
+template <bool SMALL>
 __global__ void __launch_bounds__(NTHR, 1)
     k_cg(const __grid_constant__ CUtensorMap mhi, const __grid_constant__ CUtensorMap mlo,
          ChainView c, PersistentArgs pa, const double* phi, const double2* chi, double2* x) {
     extern __shared__ __align__(1024) uint8_t dyn[];
     __shared__ f64::Smem sm64;
     TcState st;
-    tc_setup(st, dyn, c.status);
+    persistent_setup<SMALL>(st, dyn, c.status);
+    __shared__ ClusterSync s_cs;
     Team tm = make_team(c);
+    cluster_begin(pa, &s_cs, c.status);
     set_phases(c, tm, phi);
     MixedResult res{};
     bool ok = team_barrier(tm);
-    if (ok) ok = cg_mixed(c, tm, st, sm64, &mhi, &mlo, pa, chi, x, res);
+    if (ok) ok = cg_mixed<SMALL>(c, tm, st, sm64, &mhi, &mlo, pa, &s_cs, chi, x, res);
     if (ok && tm.rank == 0 && threadIdx.x == 0) {
         c.scalars[0] = res.iterations;
         c.scalars[1] = res.true_res;
         c.scalars[2] = res.status;
         c.scalars[3] = res.reliable_updates;
     }
-    tc_teardown(st);
+    persistent_teardown<SMALL>(st);
+    if (pa.cluster > 1) cluster_barrier_all();   // no member leaves while others may push
 }
 
 // One HMC trajectory with the mixed solver (same steps as the FP64 one),
 // run by team `tm`; results in c.scalars.  Returns false if the team failed.
+template <bool SMALL>
 __device__ bool run_trajectory(const ChainView& c, Team& tm, TcState& st, f64::Smem& sm64,
                                const CUtensorMap* mhi, const CUtensorMap* mlo,
-                               const PersistentArgs& pa, const TrajArgs& a) {
+                               const PersistentArgs& pa, ClusterSync* ics, const TrajArgs& a) {
     double* phi = a.phi;
     const double inv_dU = 1.0 / (c.delta * c.U);
     const double rsqrt2 = 0.70710678118654752440;
@@ -511,7 +654,7 @@ __device__ bool run_trajectory(const ChainView& c, Team& tm, TcState& st, f64::S
             if (!(ok = team_barrier(tm))) break;
         }
         MixedResult res{};
-        if (!(ok = cg_mixed(c, tm, st, sm64, mhi, mlo, pa, c.chi, c.x, res))) break;
+        if (!(ok = cg_mixed<SMALL>(c, tm, st, sm64, mhi, mlo, pa, ics, c.chi, c.x, res))) break;
         iters += res.iterations;
         rus += res.reliable_updates;
         ++solves;
@@ -557,6 +700,7 @@ __device__ bool run_trajectory(const ChainView& c, Team& tm, TcState& st, f64::S
     return ok;
 }
 
+template <bool SMALL>
 __global__ void __launch_bounds__(NTHR, 1)
     k_trajectory(const __grid_constant__ CUtensorMap mhi,
                  const __grid_constant__ CUtensorMap mlo, ChainView c, PersistentArgs pa,
@@ -564,10 +708,13 @@ __global__ void __launch_bounds__(NTHR, 1)
     extern __shared__ __align__(1024) uint8_t dyn[];
     __shared__ f64::Smem sm64;
     TcState st;
-    tc_setup(st, dyn, c.status);
+    persistent_setup<SMALL>(st, dyn, c.status);
+    __shared__ ClusterSync s_cs;
     Team tm = make_team(c);
-    run_trajectory(c, tm, st, sm64, &mhi, &mlo, pa, a);
-    tc_teardown(st);
+    cluster_begin(pa, &s_cs, c.status);
+    run_trajectory<SMALL>(c, tm, st, sm64, &mhi, &mlo, pa, &s_cs, a);
+    persistent_teardown<SMALL>(st);
+    if (pa.cluster > 1) cluster_barrier_all();   // no member leaves while others may push
 }
 
 // ---------------------------------------------------------------- batched
@@ -609,13 +756,17 @@ __global__ void __launch_bounds__(NTHR, 1)
         tm.bar = it.v.bar;
         tm.status = it.v.status;
         tm.partials = it.v.partials;
-        tm.slot = 0;
+        tm.cs = nullptr;
         st.status = it.v.status;
         TrajArgs a = it.a;
         a.seed = call->seed;
         a.traj = call->traj;
         a.phi = call->phi + it.offset;
-        const bool ok = run_trajectory(it.v, tm, st, sm64, it.maps, it.maps + 1, it.pa, a);
+        const bool ok =
+            it.pa.mode == kSmall
+                ? run_trajectory<true>(it.v, tm, st, sm64, it.maps, it.maps + 1, it.pa, nullptr, a)
+                : run_trajectory<false>(it.v, tm, st, sm64, it.maps, it.maps + 1, it.pa, nullptr,
+                                        a);
         __syncthreads();
         if (threadIdx.x == 0) {
             for (int k = 0; k < kNumScalars; ++k) outs[(size_t)ci * kNumScalars + k] = it.v.scalars[k];
@@ -721,7 +872,8 @@ int tc_ctx_init(hmc_ctx* c) {
     c->tc->ns_apply = pick_ns(v.Vr / tc::TM, v.Nt, c->num_sms);
     c->tc->n_norm = std::min(1024, std::max(1, (int)((N + 1023) / 1024)));
     const void* kernels[] = {(const void*)tc::k_apply<false>, (const void*)tc::k_apply<true>,
-                             (const void*)tc::k_cg, (const void*)tc::k_trajectory};
+                             (const void*)tc::k_cg<false>, (const void*)tc::k_trajectory<false>,
+                                 (const void*)tc::k_cg<true>, (const void*)tc::k_trajectory<true>};
     for (const void* k : kernels)
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tc::kSmemBytes) != cudaSuccess)
@@ -764,9 +916,32 @@ static int team_size(hmc_ctx* c, const void* kernel) {
     return std::max(1, std::min(g, want));
 }
 
+// Cluster size of the small-lattice CUDA-core mode: inner_ctas when given,
+// else the largest of 8, 4, 2, 1 that fits (each CTA at least 2 slices).
+static int small_cluster(const hmc_ctx* c) {
+    const ChainView& v = c->view;
+    if (c->params.inner_ctas > 0)
+        return tc::small_feasible(v.V, v.Nt, c->params.inner_ctas) ? c->params.inner_ctas : 0;
+    for (int C = 8; C >= 1; C >>= 1)
+        if ((C == 1 || v.Nt >= 2 * C) && tc::small_feasible(v.V, v.Nt, C)) return C;
+    return 0;
+}
+
 static tc::PersistentArgs persistent_args(hmc_ctx* c, int grid, double tol, int max_iter) {
     tc::PersistentArgs pa;
     const ChainView& v = c->view;
+    if (c->params.operand_mode == 3) {
+        // CUDA-core cluster solver; grid is a multiple of the cluster size
+        pa.mode = tc::kSmall;
+        pa.inner = small_cluster(c);
+        pa.ns_tile = 8;
+        pa.vec_resident = 0;
+        pa.tol = tol;
+        pa.max_iter = max_iter;
+        pa.ru_delta = c->params.ru_delta;
+        pa.cluster = 0;
+        return pa;
+    }
     // inner team: one CTA while the whole lattice fits in a handful of tiles
     // (a single CTA needs no inter-CTA barrier), else the whole launch
     const int nti = v.Vr / tc::TM;
@@ -780,11 +955,16 @@ static tc::PersistentArgs persistent_args(hmc_ctx* c, int grid, double tol, int 
     if (pa.mode == tc::kResident && !can_resident) pa.mode = tc::kStreaming;
     pa.vec_resident = 0;
     if (pa.mode == tc::kResident) {
+        // one CTA per site block, or (inner_ctas) a multiple of that: the
+        // extra CTAs take further slice tiles of the same block
         pa.inner = nti;
-        pa.ns_tile = std::min(16, pick_ns(1, v.Nt, 1));
+        if (c->params.inner_ctas > nti)
+            pa.inner = std::min(c->params.inner_ctas / nti, grid / nti) * nti;
+        pa.ns_tile = std::min(16, pick_ns(1, v.Nt, pa.inner / nti));
         const size_t free_bytes =
             tc::kOperandBytes - (size_t)nk * tc::kAChunkBytes - tc::kMaxStages * tc::kBStageSmall;
-        pa.vec_resident = (nti == 1 && 6 * sizeof(float2) * (size_t)v.N <= free_bytes) ? 1 : 0;
+        pa.vec_resident =
+            (pa.inner == 1 && 6 * sizeof(float2) * (size_t)v.N <= free_bytes) ? 1 : 0;
     } else {
         pa.inner = nti * ((v.Nt + 31) / 32) <= 2 ? 1 : grid;
         if (c->params.inner_ctas > 0) pa.inner = std::min(c->params.inner_ctas, grid);
@@ -795,33 +975,86 @@ static tc::PersistentArgs persistent_args(hmc_ctx* c, int grid, double tol, int 
     pa.tol = tol;
     pa.max_iter = max_iter;
     pa.ru_delta = c->params.ru_delta;
+    pa.cluster = 0;
     return pa;
+}
+
+// Cooperative launch of a persistent kernel.  An inner team of 2..8 CTAs
+// that divides the grid is launched as thread-block clusters (cluster 0 is
+// the inner team) unless cluster_mode says never; in automatic mode a
+// refused cluster launch falls back to global-memory team barriers.
+// `pa` is the object args points at.
+static int launch_persistent(hmc_ctx* c, const void* fn, int grid, void** args,
+                             tc::PersistentArgs& pa, cudaStream_t s) {
+    int cm = c->params.cluster_mode;
+    if (pa.mode == tc::kSmall) {
+        // the small mode reads its peers' shared memory: a cluster or nothing
+        if (pa.inner < 1 || grid % pa.inner != 0) return HMC_ERR_UNSUPPORTED;
+        if (pa.inner > 1) {
+            if (cm == 2) return HMC_ERR_UNSUPPORTED;
+            cm = 1;
+        }
+    }
+    const bool want = cm != 2 && pa.inner > 1 && pa.inner <= 8 && grid % pa.inner == 0;
+    if (cm == 1 && !want) return HMC_ERR_UNSUPPORTED;
+    if (want) {
+        pa.cluster = pa.inner;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(tc::NTHR);
+        cfg.dynamicSmemBytes = tc::kSmemBytes;
+        cfg.stream = s;
+        cudaLaunchAttribute at[2];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        at[1].id = cudaLaunchAttributeClusterDimension;
+        at[1].val.clusterDim.x = (unsigned)pa.inner;
+        at[1].val.clusterDim.y = 1;
+        at[1].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 2;
+        if (cudaLaunchKernelExC(&cfg, fn, args) == cudaSuccess) return HMC_OK;
+        (void)cudaGetLastError();   // a refused configuration is not sticky
+        pa.cluster = 0;
+        if (cm == 1) return HMC_ERR_UNSUPPORTED;
+    }
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(tc::NTHR), args, tc::kSmemBytes, s) ==
+                   cudaSuccess
+               ? HMC_OK
+               : HMC_ERR_CUDA;
+}
+
+// Small mode: the launch is a whole number of clusters.
+static int round_grid(const tc::PersistentArgs& pa, int grid) {
+    if (pa.mode != tc::kSmall || pa.inner < 1) return grid;
+    return std::max(pa.inner, grid / pa.inner * pa.inner);
 }
 
 int tc_cg(hmc_ctx* c, const double* phi, const double2* chi, double2* x, double tol,
           int max_iter, cudaStream_t s) {
-    const int grid = team_size(c, (const void*)tc::k_cg);
+    int grid = team_size(c, (const void*)tc::k_cg<false>);
     if (grid < 1) return HMC_ERR_CUDA;
     tc::PersistentArgs pa = persistent_args(c, grid, tol, max_iter);
+    if (pa.mode == tc::kSmall && pa.inner < 1) return HMC_ERR_UNSUPPORTED;
+    grid = round_grid(pa, grid);
+    const void* fn = pa.mode == tc::kSmall ? (const void*)tc::k_cg<true> : (const void*)tc::k_cg<false>;
     ChainView v = c->view;
     void* args[] = {&c->tc->map_hi, &c->tc->map_lo, &v, &pa, &phi, &chi, &x};
-    return cudaLaunchCooperativeKernel((const void*)tc::k_cg, dim3(grid), dim3(tc::NTHR), args,
-                                       tc::kSmemBytes, s) == cudaSuccess
-               ? HMC_OK
-               : HMC_ERR_CUDA;
+    return launch_persistent(c, fn, grid, args, pa, s);
 }
 
 int tc_trajectory(hmc_ctx* c, const TrajArgs& a, cudaStream_t s) {
-    const int grid = team_size(c, (const void*)tc::k_trajectory);
+    int grid = team_size(c, (const void*)tc::k_trajectory<false>);
     if (grid < 1) return HMC_ERR_CUDA;
     tc::PersistentArgs pa = persistent_args(c, grid, a.tol, a.max_iter);
+    if (pa.mode == tc::kSmall && pa.inner < 1) return HMC_ERR_UNSUPPORTED;
+    grid = round_grid(pa, grid);
+    const void* fn = pa.mode == tc::kSmall ? (const void*)tc::k_trajectory<true>
+                                           : (const void*)tc::k_trajectory<false>;
     ChainView v = c->view;
     TrajArgs av = a;
     void* args[] = {&c->tc->map_hi, &c->tc->map_lo, &v, &pa, &av};
-    return cudaLaunchCooperativeKernel((const void*)tc::k_trajectory, dim3(grid),
-                                       dim3(tc::NTHR), args, tc::kSmemBytes, s) == cudaSuccess
-               ? HMC_OK
-               : HMC_ERR_CUDA;
+    return launch_persistent(c, fn, grid, args, pa, s);
 }
 
 
@@ -911,6 +1144,7 @@ int tc_batch_create(const hmc_params* p, int n, TcBatch** out) {
         it.v.E_hi = lv.E_hi;
         it.v.E_lo = lv.E_lo;
         it.pa.inner = 1;
+        it.pa.cluster = 0;
         {
             // one CTA per chain: E resident when the chain has one site block
             const int nti = it.v.Vr / tc::TM, nk = it.v.Vp / tc::KCH;
@@ -925,6 +1159,11 @@ int tc_batch_create(const hmc_params* p, int n, TcBatch** out) {
                 const size_t free_bytes = tc::kOperandBytes - (size_t)nk * tc::kAChunkBytes -
                                           tc::kMaxStages * tc::kBStageSmall;
                 it.pa.vec_resident = 6 * sizeof(float2) * (size_t)it.v.N <= free_bytes;
+            }
+            // operand_mode 3: the CUDA-core solver on the chain's one CTA
+            if (c->params.operand_mode == 3 && tc::small_feasible(it.v.V, it.v.Nt, 1)) {
+                it.pa.mode = tc::kSmall;
+                it.pa.vec_resident = 0;
             }
         }
         it.pa.tol = c->params.cg_tol;

@@ -64,14 +64,16 @@ struct TileBars {
 constexpr size_t kSmemBytes = kOperandBytes + sizeof(TileBars) + 1024;  // + alignment slack
 
 // Operand layouts of the dynamic shared memory (1024-byte aligned base);
-// four ring stages in both:
+// four ring stages in the two tensor-core layouts:
 //   streaming: stage s holds E_hi/E_lo chunk (32 KB) at s*32K and the B
 //              stage (16 KB, N <= 64) at 128K + s*16K; E streamed by TMA
 //   resident:  E_hi/E_lo of all nk K chunks of the CTA's site block at
 //              kc*32K (loaded once per solve), B stages (8 KB, N <= 32) at
 //              nk*32K + s*8K; the rest of the area can hold the FP32 CG
 //              vectors of a chain that one CTA solves alone
-enum OperandMode : int { kStreaming = 0, kResident = 1 };
+//   small:     no tensor-core tiles; the CUDA-core cluster solver of
+//              small_cg.cuh lays out E^T and its vectors in the area
+enum OperandMode : int { kStreaming = 0, kResident = 1, kSmall = 2 };
 
 __device__ __forceinline__ uint8_t* smem_base(uint8_t* dyn) {
     const uint32_t a = smem_u32(dyn);
@@ -334,15 +336,33 @@ __device__ inline void tc_teardown(TcState& st) {
     if ((threadIdx.x >> 5) == 0) tmem_dealloc(b.tmem_base, kTmemCols);
 }
 
-// Scale 2^e with |v| 2^e in [2^12, 2^13) for a vector of squared norm n2.
+// Scale 2^e with |v| 2^e in [2^12, 2^13) for a vector of squared norm n2:
+// with n2 in [2^k, 2^(k+1)), |v| is in [2^(k/2), 2^((k+1)/2)), so
+// e = 12 - floor(k / 2), clamped to [-120, 120]; e = 0 for a zero, negative
+// or non-finite n2.  Integer operations on the bits of n2 only.
 __device__ __forceinline__ void vector_scale(double n2, float& scale, float& inv) {
+    const long long bits = __double_as_longlong(n2);
+    const int ex = (int)((bits >> 52) & 0x7ff);
     int e = 0;
-    if (n2 > 0.0 && isfinite(n2)) {
-        e = 12 - ilogb(sqrt(n2));
+    if (bits > 0 && ex != 0x7ff) {
+        e = 12 - ((ex - 1023) >> 1);   // arithmetic shift: floor division by 2
         e = max(-120, min(120, e));
     }
-    scale = ldexpf(1.f, e);
-    inv = ldexpf(1.f, -e);
+    scale = __int_as_float((127 + e) << 23);
+    inv = __int_as_float((127 - e) << 23);
+}
+
+// The same scale from an FP32 squared norm (exponent field of 8 bits).
+__device__ __forceinline__ void vector_scale_f(float n2, float& scale, float& inv) {
+    const int bits = __float_as_int(n2);
+    const int ex = (bits >> 23) & 0xff;
+    int e = 0;
+    if (bits > 0 && ex != 0xff) {
+        e = 12 - ((ex - 127) >> 1);
+        e = max(-120, min(120, e));
+    }
+    scale = __int_as_float((127 + e) << 23);
+    inv = __int_as_float((127 - e) << 23);
 }
 
 // One output tile: target slices t0 .. t0+ns-1 (ns <= NMAX/2), sites

@@ -18,3 +18,20 @@ def test_candidates_cover_one_cta_and_tile_teams():
 def test_pick_fastest_then_fewest_ctas():
     t = [((12, 4, 8, 1), 2.0e-5), ((12, 1, 32, 2), 2.3e-5), ((4, 4, 8, 1), 2.0e-5)]
     assert autotune.pick(t) == (4, 4, 8, 1)
+
+
+def test_small_cluster_mode_candidates():
+    """CUDA-core cluster mode (operand_mode 3): clusters of 1, 2, 4, 8 CTAs with
+    at most 16 slices each and the layout inside the 204 KB operand area."""
+    c = autotune.candidates(hmc.Params(L=6, Nt=32, beta=4.0), num_sms=148)
+    small = [s for s in c if s[3] == 3]
+    assert (8, 8, 8, 3) in small and (2, 2, 8, 3) in small
+    assert all(team % inner == 0 for team, inner, _, _ in small)
+    assert not any(inner == 1 for _, inner, _, _ in small)     # 32 slices on one CTA
+    assert autotune.small_feasible(72, 32, 8)
+    assert not autotune.small_feasible(72, 32, 1)
+    assert autotune.small_feasible(128, 64, 8)                   # L = 8
+    assert not autotune.small_feasible(1152, 96, 8)              # L = 24: E^T too large
+    assert not autotune.small_feasible(18, 4, 8)                 # fewer slices than CTAs
+    big = autotune.candidates(hmc.Params(L=24, Nt=96, beta=12.0), num_sms=148)
+    assert not any(mode == 3 for *_, mode in big)

@@ -489,7 +489,8 @@ def run_batch(args):
         from paper_2210_06874_gb300 import autotune
         tuned = [autotune.tune(p, single_cta=True) for p in plist]
         for p in tuned:
-            shapes["L%d_Nt%d" % (p.L, p.Nt)] = p.tile_slices
+            shapes["L%d_Nt%d" % (p.L, p.Nt)] = {"tile_slices": p.tile_slices,
+                                                "operand_mode": p.operand_mode}
         loop_params = [autotune.tune(p) for p in plist[:args.loop_chains]]
         plist = tuned
     else:
@@ -552,7 +553,7 @@ def run_batch(args):
                    "Nt_set": sorted(set(p.Nt for p in plist)),
                    "thermalisation_trajectories": n_therm,
                    "step": "one trajectory of every chain in one persistent launch (CUDA graph)",
-                   "tile_slices_by_autotuner": shapes or "automatic",
+                   "shape_by_autotuner": shapes or "automatic",
                    "l2": "inputs (all chains' fields and workspaces) exceed one trajectory's "
                          "reuse window; no flush"},
         "loop_of_single_chain_launches": {

@@ -30,8 +30,8 @@ def small_feasible(V, Nt, C):
     G = Vr // 32
     KS = min(1 if G >= 8 else 8 // G, V)
     r16 = lambda b: (b + 15) // 16 * 16
-    total = (r16(V * Vr * 4) + 5 * r16(S * V * 8) + r16((S + 1) * V * 8) +
-             2 * r16(V * SP * 8) + 2 * r16(V * 8) + r16(KS * S * Vr * 8))
+    total = (r16(V * Vr * 4) + 6 * r16(S * V * 8) + 2 * r16(V * SP * 8) + 2 * r16(V * 8) +
+             r16(KS * S * Vr * 8))
     return total <= 204 * 1024
 
 

@@ -103,6 +103,13 @@ struct ClusterSync {
     unsigned count;                        // syncs this CTA has completed
     double part[2][kMaxCluster][kVals];    // FP64 sums: [k & 1][member][value]
     float part_f[2][kMaxCluster];          // FP32 sums: [k & 1][member]
+    // Byte-counted exchanges (st.async / bulk copies with mbarrier
+    // complete_tx): phase k uses bar_tx[k & 1], armed by this CTA's own
+    // arrive.expect_tx; the data itself completes the phase, so the senders
+    // need no release fence.
+    uint64_t bar_tx[2];
+    unsigned count_tx;
+    float part_tx[2][kMaxCluster];
 };
 
 struct Team {
@@ -174,11 +181,16 @@ __device__ __forceinline__ void cluster_barrier_all() {
 // member arrives remotely on a barrier that is not yet initialised.
 __device__ inline void cluster_sync_init(ClusterSync* cs, int size) {
     if (threadIdx.x == 0) {
-        for (int b = 0; b < 2; ++b)
+        for (int b = 0; b < 2; ++b) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(cta_smem_u32(&cs->bar[b])),
                          "r"(size)
                          : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(
+                             cta_smem_u32(&cs->bar_tx[b]))
+                         : "memory");
+        }
         cs->count = 0;
+        cs->count_tx = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();

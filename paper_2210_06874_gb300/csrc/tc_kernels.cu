@@ -407,45 +407,51 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
     volatile double* seg = c.scalars + 12;   // [0] end reason, [1] iterations
     for (;;) {
         if (SMALL && in_inner) {
-            // small lattice: contractions overlapped with the cluster sums
-            __shared__ SplitSum s_ss;
+            // small lattice: each half iteration is epilogue -> partial norm
+            // out -> contraction -> boundary column out -> wait (byte-counted)
+            __shared__ SmallSum s_ss;
             int reason = 0;
             if (refresh) {
                 small_refresh_r(sm, c.r);
                 refresh = false;
             }
             __syncthreads();
-            small_prime(sm);
-            if (!team_barrier(ti)) return false;   // halos pushed, operands written
+            small_load_ud(sm);
+            __syncthreads();
             small_matvec_any(sm, sm.v(sm.l.ud));
             __syncthreads();
-            small_matvec_col(sm, sm.v(sm.l.hr), sm.S - 1);
-            __syncthreads();
+            small_send_boundary_plain(sm);
+            if (!team_barrier(ti)) return false;   // boundary columns published
+            unsigned kk = ti.cs ? ti.cs->count_tx : 0u;   // exchange phase
+            const uint32_t xbytes = (uint32_t)(4 * ti.size + 8 * c.V);
             if (s_cg.it >= pa.max_iter) reason = kSegMaxIter;
             while (reason == 0) {
-                // q = M^dag p' (p' = r + beta p); E (e^{i phi} q) overlaps |q|^2
                 float qq, rr_new;
-                sum_begin(ti, s_ss, small_dag_epilogue(sm, s_cg.beta));
+                // q = M^dag p', p' = r + beta p; then E e^{i phi} q
+                small_sum_begin(ti, s_ss, kk, small_dag_epilogue(sm, s_cg.beta));
                 small_matvec_any(sm, sm.v(sm.l.um));
-                if (!sum_end(ti, s_ss, qq)) return false;
+                __syncthreads();
+                small_send_boundary(sm, ti.cs, kk, sm.S - 1, sm.l.bm, sm.next);
+                if (!small_sum_end(ti, s_ss, kk, xbytes, qq)) return false;
+                ++kk;
                 if (threadIdx.x == 0) cg_after_q(s_cg, qq);
                 __syncthreads();
                 if (s_cg.reason != 0) { reason = s_cg.reason; break; }
-                small_matvec_col(sm, sm.v(sm.l.hq), 0);
-                __syncthreads();
-                // x += alpha p', r -= alpha M q; E r overlaps |r|^2
-                sum_begin(ti, s_ss, small_m_epilogue(sm, s_cg.alpha));
+                // x += alpha p', r -= alpha M q; then E r
+                small_sum_begin(ti, s_ss, kk, small_m_epilogue(sm, s_cg.alpha));
                 small_matvec_any(sm, sm.v(sm.l.ud));
-                if (!sum_end(ti, s_ss, rr_new)) return false;
+                __syncthreads();
+                small_send_boundary(sm, ti.cs, kk, 0, sm.l.bd, sm.prev);
+                if (!small_sum_end(ti, s_ss, kk, xbytes, rr_new)) return false;
+                ++kk;
                 if (threadIdx.x == 0) {
                     cg_after_r(s_cg, rr_new);
                     if (s_cg.reason == 0 && s_cg.it >= pa.max_iter) s_cg.reason = kSegMaxIter;
                 }
                 __syncthreads();
                 if (s_cg.reason != 0) { reason = s_cg.reason; break; }
-                small_matvec_col(sm, sm.v(sm.l.hr), sm.S - 1);
-                __syncthreads();
             }
+            if (threadIdx.x == 0 && ti.cs) ti.cs->count_tx = kk;
             if (reason != kSegNonfinite) small_fold_x(sm, x64);
             if (tm.rank == 0 && threadIdx.x == 0) {
                 seg[0] = reason;

@@ -92,8 +92,13 @@ def tune(params, iters=40, reps=2, single_cta=False, seed=1):
                               "tile_slices": ns, "operand_mode": mode,
                               "precision": hmc.PREC_MIXED})
             ctx = hmc.Context(p)
-            ctx.cg_solve(phi, chi, tol=1e-30, max_iter=4, prec=hmc.PREC_MIXED,
-                         allow_not_converged=True)
+            try:
+                ctx.cg_solve(phi, chi, tol=1e-30, max_iter=4, prec=hmc.PREC_MIXED,
+                             allow_not_converged=True)
+            except hmc.HmcError:
+                # a launch configuration this device (or a profiler) refuses
+                ctx.close()
+                continue
             s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             stream = torch.cuda.current_stream()
             s.record(stream)

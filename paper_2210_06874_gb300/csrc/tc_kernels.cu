@@ -1010,15 +1010,18 @@ static int launch_persistent(hmc_ctx* c, const void* fn, int grid, void** args,
         cfg.blockDim = dim3(tc::NTHR);
         cfg.dynamicSmemBytes = tc::kSmemBytes;
         cfg.stream = s;
+        // the CTAs of one cluster are scheduled together, so a launch that
+        // is one cluster needs no cooperative attribute; several clusters
+        // take it for the team barriers between them
         cudaLaunchAttribute at[2];
-        at[0].id = cudaLaunchAttributeCooperative;
-        at[0].val.cooperative = 1;
-        at[1].id = cudaLaunchAttributeClusterDimension;
-        at[1].val.clusterDim.x = (unsigned)pa.inner;
-        at[1].val.clusterDim.y = 1;
-        at[1].val.clusterDim.z = 1;
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)pa.inner;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        at[1].id = cudaLaunchAttributeCooperative;
+        at[1].val.cooperative = 1;
         cfg.attrs = at;
-        cfg.numAttrs = 2;
+        cfg.numAttrs = grid == pa.inner ? 1 : 2;
         if (cudaLaunchKernelExC(&cfg, fn, args) == cudaSuccess) return HMC_OK;
         (void)cudaGetLastError();   // a refused configuration is not sticky
         pa.cluster = 0;

@@ -90,7 +90,17 @@ typedef struct hmc_params {
                             of E resident for the whole solve (needs
                             V <= 256 and one CTA per 128-site block; a chain
                             with V <= 128 then keeps its FP32 CG vectors in
-                            shared memory too when they fit) */
+                            shared memory too when they fit), 3 run the FP32
+                            iterations on the CUDA cores of one thread-block
+                            cluster of inner_ctas CTAs (1..16; 0 picks the
+                            largest of 16, 8, 4, 2, 1 that fits), with E^T
+                            in FP32 and the iterates of each CTA's time
+                            slices in its shared memory: needs at most 16
+                            slices per CTA and the layout within the shared
+                            memory of a CTA (about V <= 128 at 8 slices);
+                            HMC_ERR_UNSUPPORTED otherwise, or if the device
+                            refuses the cluster (sizes above 8 are
+                            non-portable) */
     int cluster_mode;    /* mixed path, inner team of 2..8 CTAs: 0 automatic
                             (launch it as one thread-block cluster, whose
                             barriers and sums go through distributed shared

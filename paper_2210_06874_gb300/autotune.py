@@ -20,9 +20,9 @@ _cache = {}
 
 def small_feasible(V, Nt, C):
     """Host copy of the feasibility rule of the CUDA-core cluster mode
-    (operand_mode 3): 1 <= C <= 8 CTAs, each with 1..16 time slices, and the
+    (operand_mode 3): 1 <= C <= 16 CTAs, each with 1..16 time slices, and the
     shared-memory layout within the 204 KB operand area."""
-    if C < 1 or C > 8 or Nt < C or -(-Nt // C) > 16:
+    if C < 1 or C > 16 or Nt < C or -(-Nt // C) > 16:
         return False
     S = -(-Nt // C)
     Vr = -(-V // 32) * 32
@@ -39,13 +39,15 @@ def candidates(params, num_sms, single_cta=False):
     """Shapes (team_ctas, inner_ctas, tile_slices, operand_mode) worth timing:
     streamed E with one CTA or teams sized to the tensor-core / FP64 tile
     counts, resident E (one CTA per 128-site block) where E fits, and the
-    CUDA-core cluster mode (clusters of 1, 2, 4 or 8 CTAs) where it fits."""
+    CUDA-core cluster mode (clusters of 1, 2, 4, 8 or 16 CTAs) where it fits;
+    16 is a non-portable cluster size that a device may refuse (the tuner
+    then skips it)."""
     V, Nt = params.V, params.Nt
     nti = (V + 127) // 128
     vp = ((V + 63) // 64) * 64
     f64_tiles = ((V + 31) // 32) * ((Nt + 7) // 8)
     out = []
-    for C in (1, 2, 4, 8):
+    for C in (1, 2, 4, 8, 16):
         if single_cta and C > 1:
             break
         if small_feasible(V, Nt, C):

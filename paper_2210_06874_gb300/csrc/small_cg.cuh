@@ -33,7 +33,7 @@ namespace hmc {
 namespace tc {
 
 constexpr int kSmallMaxSlices = 16;    // time slices per CTA
-constexpr int kSmallMaxCluster = 8;    // CTAs per cluster (portable size)
+constexpr int kSmallMaxCluster = 16;   // CTAs per cluster (above 8: non-portable size)
 
 // Shared-memory layout (byte offsets into the operand area; every CTA of the
 // cluster uses the same offsets, so a peer's buffer is at the same offset).
@@ -84,7 +84,7 @@ __host__ __device__ inline SmallLayout small_layout(int V, int Nt, int C) {
     return l;
 }
 
-// The cluster layout fits: C in [1, 8], every CTA owns 1..16 slices, and
+// The cluster layout fits: C in [1, 16], every CTA owns 1..16 slices, and
 // the buffers fit the operand area.
 __host__ __device__ inline bool small_feasible(int V, int Nt, int C) {
     if (C < 1 || C > kSmallMaxCluster || Nt < C) return false;

@@ -884,6 +884,12 @@ int tc_ctx_init(hmc_ctx* c) {
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tc::kSmemBytes) != cudaSuccess)
             return HMC_ERR_CUDA;
+    // the small-lattice mode may run on clusters of up to 16 CTAs (beyond the
+    // portable 8); a device that cannot co-schedule them refuses the launch
+    for (const void* k : {(const void*)tc::k_cg<true>, (const void*)tc::k_trajectory<true>})
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess)
+            (void)cudaGetLastError();
     return HMC_OK;
 }
 
@@ -928,7 +934,7 @@ static int small_cluster(const hmc_ctx* c) {
     const ChainView& v = c->view;
     if (c->params.inner_ctas > 0)
         return tc::small_feasible(v.V, v.Nt, c->params.inner_ctas) ? c->params.inner_ctas : 0;
-    for (int C = 8; C >= 1; C >>= 1)
+    for (int C = 16; C >= 1; C >>= 1)
         if ((C == 1 || v.Nt >= 2 * C) && tc::small_feasible(v.V, v.Nt, C)) return C;
     return 0;
 }
@@ -1001,7 +1007,8 @@ static int launch_persistent(hmc_ctx* c, const void* fn, int grid, void** args,
             cm = 1;
         }
     }
-    const bool want = cm != 2 && pa.inner > 1 && pa.inner <= 8 && grid % pa.inner == 0;
+    const int max_cluster = pa.mode == tc::kSmall ? tc::kSmallMaxCluster : 8;
+    const bool want = cm != 2 && pa.inner > 1 && pa.inner <= max_cluster && grid % pa.inner == 0;
     if (cm == 1 && !want) return HMC_ERR_UNSUPPORTED;
     if (want) {
         pa.cluster = pa.inner;

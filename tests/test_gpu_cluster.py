@@ -177,3 +177,25 @@ def test_small_cluster_mode_refusals(kw):
     with pytest.raises(hmc.HmcError) as ei:
         c.cg_solve(phi, chi, tol=1e-10, prec=hmc.PREC_MIXED)
     assert ei.value.code == -6
+
+
+@pytest.mark.parametrize("L,Nt", [(6, 32), (8, 64), (5, 23)])
+def test_cg_small_cluster_of_16(L, Nt):
+    """A cluster of 16 CTAs (non-portable size; skipped where the device
+    refuses it): 2 to 4 slices per CTA, ragged at Nt = 23."""
+    beta, U = 0.125 * Nt, 3.5
+    V = 2 * L * L
+    phi = synth.gaussian_field(71 + L, Nt, V, beta / Nt * U, scale=0.5)
+    chi = synth.complex_gaussian(72 + L, Nt, V)
+    c = hmc.Context(hmc.Params(L=L, Nt=Nt, beta=beta, U=U, team_ctas=16, inner_ctas=16,
+                               operand_mode=3))
+    try:
+        x, st = c.cg_solve(dev(phi), dev(chi), tol=1e-10, prec=hmc.PREC_MIXED)
+    except hmc.HmcError as e:
+        if e.code == -6:
+            pytest.skip("device refuses a cluster of 16 CTAs")
+        raise
+    assert st.status == 0 and st.true_residual <= 1e-10
+    E = oracle_E(L, Nt, beta)
+    res = chi - ops.apply_MMdag(E, phi, x.cpu().numpy())
+    assert np.linalg.norm(res) / np.linalg.norm(chi) < 1.2e-10

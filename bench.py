@@ -27,6 +27,9 @@ sys.path.insert(0, ROOT)
 METRIC = ("HMC trajectories/s and M-applications/s (frac. of roofline), "
           "mixed vs FP64 at equal tol")
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# dram__bytes_read.sum + dram__bytes_write.sum of one trajectory launch in the
+# CUDA-core cluster mode, by (workload, cluster size), from ncu
+CAPTURED_TRAFFIC = {("l6_nt32", 16): 247552}
 # FP32 FMA peak of the whole GPU from unit counts and the maximum SM clock
 FP32_FMA_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
@@ -342,8 +345,13 @@ def run_ours(args):
                 "peak_source": "measured cuBLAS DGEMM 4096^3 on this GPU (FP64 ALU peak)"}
     elif params.operand_mode == 3:
         peak = FP32_FMA_TFLOPS
+        # DRAM bytes of one k_trajectory<1> launch from the ncu capture in
+        # profiles/k_trajectory_small_l6_nt32_full.md (that workload and
+        # cluster size only; null elsewhere)
+        traffic = (CAPTURED_TRAFFIC.get((name, params.inner_ctas))
+                   if params.team_ctas == params.inner_ctas else None)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
                 "peak_source": "FP32 FMA rate from unit counts: 152 SMs x 128 lanes x 2 flop "
                                "x 2.07 GHz (the CUDA-core cluster mode runs on one cluster)"}
     else:

@@ -427,20 +427,37 @@ def run_apply(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     flush_acc = torch.empty((), dtype=torch.float32, device=dev)
-    clocks = ClockSampler(local_rank)
+    # the applications of a step, captured once through the C ABI into a CUDA
+    # graph: its replay times the GPU work without the per-call host cost
+    graph = torch.cuda.CUDAGraph()
     torch.cuda.synchronize()
+    with torch.cuda.graph(graph):
+        for _ in range(args.applies):
+            ctx.apply_M(phi, psi, out, prec=p)
+    graph.replay()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
     clocks.start()
     total_ms = 0.0
     for _ in range(args.steps):
         flush_l2(flush, flush_acc)
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record(stream)
-        for _ in range(args.applies):
-            ctx.apply_M(phi, psi, out, prec=p)
+        graph.replay()
         e.record(stream)
         e.synchronize()
         total_ms += s.elapsed_time(e)
     clk = clocks.stop()
+    # the same applications called one by one from Python (host-bound for
+    # small lattices)
+    flush_l2(flush, flush_acc)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    for _ in range(args.applies):
+        ctx.apply_M(phi, psi, out, prec=p)
+    e.record(stream)
+    e.synchronize()
+    eager_ms = s.elapsed_time(e) / args.applies
     n = args.steps * args.applies
     per_ms = total_ms / n
     flop = flops_per_apply(V, Nt)
@@ -469,7 +486,9 @@ def run_apply(args):
             "data": "synthetic",
             "config": {"workload": name, "mode": "apply", "precision": prec, "V": V, "Nt": Nt,
                        "applies_per_step": args.applies,
+                       "timing": "one CUDA-graph replay of the step's C-ABI calls",
                        "l2": "flushed (256 MB write + read sweep) between timed steps"},
+            "per_call_from_python_us": eager_ms * 1e3,
             "gpu_launches": n * 2 if prec != "fp64" else n * 2,
             "roofline": roof, "clocks": clk}
     if rank == 0:

@@ -25,7 +25,6 @@ struct ChainView {
     double *pi, *phi_old;       // double [Nt][V]
     // FP32 workspaces for the mixed path, float2 [Nt][V] each
     float2 *cis_f, *r_f, *p_f, *p2_f, *q_f, *x_f;
-    double* norm_partials;      // per-CTA partial |v|^2 of standalone applies
     // team synchronisation
     unsigned* bar;              // 2 words
     int* status;                // device status word

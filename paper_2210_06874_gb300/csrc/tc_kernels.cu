@@ -20,7 +20,15 @@ namespace hmc {
 struct TcCtx {
     CUtensorMap map_hi, map_lo;
     int ns_apply;        // slices per tile of standalone applications
-    int n_norm;          // CTAs of the norm pre-pass
+    // pre-split B operand of standalone applications: FP16 hi / lo rows
+    // [2 Nt + 64][Vp] (row 2t: re, 2t+1: im of the source of target slice t;
+    // the last 64 rows stay zero for tiles that run past Nt) and the
+    // per-slice inverse scales
+    CUtensorMap map_bhi, map_blo;
+    __half* bhi;
+    __half* blo;
+    float* inv_col;
+    int b_rows;
 };
 
 namespace tc {
@@ -162,48 +170,86 @@ __device__ bool apply_team(const ChainView& c, const Team& tm, TcState& st,
 }
 
 // ---------------------------------------------------------------- standalone
-// cis_f = exp(i phi) in FP32 and per-CTA partial |in|^2.
-__global__ void k_prep(const double* __restrict__ phi, float2* __restrict__ cis_f,
-                       const float2* __restrict__ in, double* __restrict__ partials, int N) {
-    double acc[1] = {0.0};
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < N; e += gridDim.x * blockDim.x) {
-        float s, co;
-        sincosf((float)phi[e], &s, &co);
-        cis_f[e] = make_float2(co, s);
-        const float2 v = in[e];
-        acc[0] += (double)v.x * v.x + (double)v.y * v.y;
+// B operand of one standalone application, split before the tiles run: for
+// target slice t (one block) the source u = in_{t+1} (M^dag) or
+// e^{i phi_{t-1}} in_{t-1} (M), scaled by 2^e with max |Re u|, |Im u| in
+// [2^14, 2^15), written as FP16 hi = fp16(s u) and lo = fp16((s u - hi) 2^11)
+// in rows 2t (re) and 2t+1 (im), zero from V to Vp; inv[t] = 2^-e.  Also
+// writes the FP32 phase table of slice t (the M^dag epilogue reads it).
+// Dynamic shared memory: V float2 (the source slice).
+template <bool DAG>
+__global__ void __launch_bounds__(256)
+    k_split(const double* __restrict__ phi, const float2* __restrict__ in,
+            float2* __restrict__ cis_f, __half* __restrict__ bhi, __half* __restrict__ blo,
+            float* __restrict__ inv, int V, int Vp, int Nt) {
+    extern __shared__ float2 u_s[];
+    __shared__ float s_max[8];
+    __shared__ int s_e;
+    const int t = blockIdx.x;
+    const int ts = DAG ? (t + 1 == Nt ? 0 : t + 1) : (t == 0 ? Nt - 1 : t - 1);
+    float mx = 0.f;
+    for (int k = threadIdx.x; k < V; k += blockDim.x) {
+        float sn, cs;
+        sincosf((float)phi[(size_t)t * V + k], &sn, &cs);
+        cis_f[(size_t)t * V + k] = make_float2(cs, sn);
+        float2 u = in[(size_t)ts * V + k];
+        if (!DAG) {
+            sincosf((float)phi[(size_t)ts * V + k], &sn, &cs);
+            u = make_float2(cs * u.x - sn * u.y, cs * u.y + sn * u.x);
+        }
+        u_s[k] = u;
+        mx = fmaxf(mx, fmaxf(fabsf(u.x), fabsf(u.y)));
     }
-    block_reduce<1>(acc);
-    if (threadIdx.x == 0) partials[blockIdx.x] = acc[0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, s_max[w]);
+        const int bits = __float_as_int(m), ex = (bits >> 23) & 0xff;
+        int e = 0;
+        if (bits > 0 && ex != 0xff) e = max(-120, min(120, 14 - (ex - 127)));
+        s_e = e;
+        inv[t] = __int_as_float((127 - e) << 23);
+    }
+    __syncthreads();
+    const float sc = __int_as_float((127 + s_e) << 23);
+    __half* hr = bhi + (size_t)(2 * t) * Vp;
+    __half* lr = blo + (size_t)(2 * t) * Vp;
+    for (int k = threadIdx.x; k < Vp; k += blockDim.x) {
+        __half h0 = __float2half_rn(0.f), h1 = h0, l0 = h0, l1 = h0;
+        if (k < V) {
+            const float2 u = u_s[k];
+            const float x = u.x * sc, y = u.y * sc;
+            h0 = __float2half_rn(x);
+            h1 = __float2half_rn(y);
+            l0 = __float2half_rn((x - __half2float(h0)) * kLoScale);
+            l1 = __float2half_rn((y - __half2float(h1)) * kLoScale);
+        }
+        hr[k] = h0;
+        hr[Vp + k] = h1;
+        lr[k] = l0;
+        lr[Vp + k] = l1;
+    }
 }
 
+// Standalone application of M or M^dag: the tiles load E and the pre-split
+// B by TMA and contract them; the epilogue forms the result.
 template <bool DAG>
 __global__ void __launch_bounds__(NTHR, 1)
     k_apply(const __grid_constant__ CUtensorMap mhi, const __grid_constant__ CUtensorMap mlo,
-            ChainView c, int ns_tile, const float2* in, float2* out, int n_norm) {
+            const __grid_constant__ CUtensorMap bhi, const __grid_constant__ CUtensorMap blo,
+            ChainView c, int ns_tile, const float2* in, float2* out, const float* inv) {
     extern __shared__ __align__(1024) uint8_t dyn[];
     TcState st;
     tc_setup(st, dyn, c.status);
-    __shared__ double s_n2;
-    if (threadIdx.x == 0) {
-        double n2 = 0.0;
-        for (int j = 0; j < n_norm; ++j) n2 += c.norm_partials[j];
-        s_n2 = n2;
-    }
-    __syncthreads();
-    float scale, inv;
-    vector_scale(s_n2, scale, inv);
     EpiStore<DAG> epi{in, out, c.cis_f, c.V, c.Nt, 0.f};
     const int nti = c.Vr / TM;
     int i0, t0, ns;
     tile_coords(blockIdx.x, nti, ns_tile, c.Nt, i0, t0, ns);
-    if (DAG) {
-        SrcPlain src{in, c.V};
-        tc_tile<DAG>(st, &mhi, &mlo, c.V, c.Nt, c.Vp, i0, t0, ns, src, scale, inv, epi);
-    } else {
-        SrcPhase src{in, c.cis_f, c.V};
-        tc_tile<DAG>(st, &mhi, &mlo, c.V, c.Nt, c.Vp, i0, t0, ns, src, scale, inv, epi);
-    }
+    SrcSplit src{&bhi, &blo, inv};
+    tc_tile<DAG>(st, &mhi, &mlo, c.V, c.Nt, c.Vp, i0, t0, ns, src, 1.f, 1.f, epi);
     tc_teardown(st);
 }
 
@@ -801,12 +847,12 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-static bool make_map(CUtensorMap* m, void* base, int Vr, int Vp) {
+static bool make_map(CUtensorMap* m, void* base, int Vr, int Vp, int box_rows = tc::TM) {
     auto enc = encode_fn();
     if (!enc) return false;
     cuuint64_t dims[2] = {(cuuint64_t)Vp, (cuuint64_t)Vr};
     cuuint64_t strides[1] = {(cuuint64_t)Vp * 2};
-    cuuint32_t box[2] = {(cuuint32_t)tc::KCH, (cuuint32_t)tc::TM};
+    cuuint32_t box[2] = {(cuuint32_t)tc::KCH, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -863,7 +909,6 @@ int tc_ctx_init(hmc_ctx* c) {
     v.p2_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
     v.q_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
     v.x_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
-    v.norm_partials = (double*)dev_alloc(c, 1024 * sizeof(double), &ok);
     if (!ok) return HMC_ERR_CUDA;
     if (cudaMemcpy(dhi, hi.data(), hi.size() * sizeof(__half), cudaMemcpyHostToDevice) !=
             cudaSuccess ||
@@ -876,7 +921,26 @@ int tc_ctx_init(hmc_ctx* c) {
     if (!make_map(&c->tc->map_hi, dhi, v.Vr, v.Vp) || !make_map(&c->tc->map_lo, dlo, v.Vr, v.Vp))
         return HMC_ERR_CUDA;
     c->tc->ns_apply = pick_ns(v.Vr / tc::TM, v.Nt, c->num_sms);
-    c->tc->n_norm = std::min(1024, std::max(1, (int)((N + 1023) / 1024)));
+    if (c->params.tile_slices > 0) c->tc->ns_apply = c->params.tile_slices;
+    {
+        // pre-split B of standalone applications (rows padded by 64 zero rows)
+        const int nb = ((2 * c->tc->ns_apply + 15) / 16) * 16;   // MMA N = TMA box rows
+        c->tc->b_rows = 2 * v.Nt + 64;
+        const size_t nbh = (size_t)c->tc->b_rows * v.Vp;
+        bool okb = true;
+        c->tc->bhi = (__half*)dev_alloc(c, nbh * sizeof(__half), &okb);
+        c->tc->blo = (__half*)dev_alloc(c, nbh * sizeof(__half), &okb);
+        c->tc->inv_col = (float*)dev_alloc(c, (size_t)v.Nt * sizeof(float), &okb);
+        if (!okb || !make_map(&c->tc->map_bhi, c->tc->bhi, c->tc->b_rows, v.Vp, nb) ||
+            !make_map(&c->tc->map_blo, c->tc->blo, c->tc->b_rows, v.Vp, nb))
+            return HMC_ERR_CUDA;
+        const int split_smem = V * (int)sizeof(float2);
+        for (const void* k : {(const void*)tc::k_split<false>, (const void*)tc::k_split<true>})
+            if (split_smem > 48 * 1024 &&
+                cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     split_smem) != cudaSuccess)
+                return HMC_ERR_CUDA;
+    }
     const void* kernels[] = {(const void*)tc::k_apply<false>, (const void*)tc::k_apply<true>,
                              (const void*)tc::k_cg<false>, (const void*)tc::k_trajectory<false>,
                                  (const void*)tc::k_cg<true>, (const void*)tc::k_trajectory<true>};
@@ -901,15 +965,21 @@ void tc_ctx_free(hmc_ctx* c) {
 int tc_apply(hmc_ctx* c, const double* phi, const float2* in, float2* out, bool dag,
              cudaStream_t s) {
     const ChainView& v = c->view;
-    tc::k_prep<<<c->tc->n_norm, 256, 0, s>>>(phi, v.cis_f, in, v.norm_partials, v.N);
     const int ns = c->tc->ns_apply;
     const int tiles = (v.Vr / tc::TM) * ((v.Nt + ns - 1) / ns);
-    if (dag)
+    const size_t split_smem = (size_t)v.V * sizeof(float2);
+    TcCtx* t = c->tc;
+    if (dag) {
+        tc::k_split<true><<<v.Nt, 256, split_smem, s>>>(phi, in, v.cis_f, t->bhi, t->blo,
+                                                        t->inv_col, v.V, v.Vp, v.Nt);
         tc::k_apply<true><<<tiles, tc::NTHR, tc::kSmemBytes, s>>>(
-            c->tc->map_hi, c->tc->map_lo, v, ns, in, out, c->tc->n_norm);
-    else
+            t->map_hi, t->map_lo, t->map_bhi, t->map_blo, v, ns, in, out, t->inv_col);
+    } else {
+        tc::k_split<false><<<v.Nt, 256, split_smem, s>>>(phi, in, v.cis_f, t->bhi, t->blo,
+                                                         t->inv_col, v.V, v.Vp, v.Nt);
         tc::k_apply<false><<<tiles, tc::NTHR, tc::kSmemBytes, s>>>(
-            c->tc->map_hi, c->tc->map_lo, v, ns, in, out, c->tc->n_norm);
+            t->map_hi, t->map_lo, t->map_bhi, t->map_blo, v, ns, in, out, t->inv_col);
+    }
     return cudaGetLastError() == cudaSuccess ? HMC_OK : HMC_ERR_CUDA;
 }
 

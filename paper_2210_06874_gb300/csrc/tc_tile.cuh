@@ -105,6 +105,7 @@ __device__ __forceinline__ int source_slice(int t, int Nt) {
 // at source slice ts and sites kb..kb+7 (kb a multiple of 8, kb + 8 <= V)
 // or at one site k.
 struct SrcPlain {                       // u = in
+    static constexpr bool kTma = false;
     const float2* in;
     int V;
     __device__ __forceinline__ void load8(int ts, int kb, float2 (&v)[8]) const {
@@ -120,6 +121,7 @@ struct SrcPlain {                       // u = in
 };
 
 struct SrcPhase {                       // u = exp(i phi) * in
+    static constexpr bool kTma = false;
     const float2* in;
     const float2* cis;
     int V;
@@ -142,6 +144,7 @@ struct SrcPhase {                       // u = exp(i phi) * in
 // u = p_new = r + beta p_old, the CG direction update done on the fly; r is
 // the FP32 iterate, or (refresh) the FP64 true residual rounded to FP32.
 struct SrcDirection {
+    static constexpr bool kTma = false;
     const float2* r;
     const double2* r64;
     const float2* p_old;
@@ -178,6 +181,18 @@ struct SrcDirection {
     __device__ __forceinline__ float2 load1(int ts, int k) const {
         return one((size_t)ts * V + k);
     }
+};
+
+// B prepared before the application (one FP16 hi/lo split per time slice,
+// rows 2t / 2t+1 = re / im of the source of target slice t, K contiguous,
+// scaled by the power of two 1 / inv[t]): the TMA warp loads it with the
+// E chunk, the producer warps only keep the barrier count, and the
+// epilogue unscales column by column.
+struct SrcSplit {
+    static constexpr bool kTma = true;
+    const CUtensorMap* bhi;
+    const CUtensorMap* blo;
+    const float* inv;
 };
 
 // Fill the B operand of K chunk [k0, k0+64) for the tile's slices t0..t0+ns-1
@@ -394,7 +409,15 @@ __device__ bool tc_tile(TcState& st, const CUtensorMap* mhi, const CUtensorMap* 
                 if (n > 0) ok = mbar_wait(smem_u32(&bars.empty[s]), (n - 1) & 1, st.status);
                 if (!ok) break;
                 const uint32_t bar = smem_u32(&bars.full[s]);
-                if (streaming) {
+                if constexpr (Src::kTma) {
+                    // streaming layout only: E and the pre-split B of chunk kc
+                    mbar_arrive_expect_tx(bar, kAChunkBytes + 2u * (uint32_t)N * 128u);
+                    tma_load_2d(smem_u32(st.a_hi(kc, s)), mhi, kc * KCH, i0, bar);
+                    tma_load_2d(smem_u32(st.a_hi(kc, s) + kATileBytes), mlo, kc * KCH, i0, bar);
+                    tma_load_2d(smem_u32(st.b_hi(s)), src.bhi, kc * KCH, 2 * t0, bar);
+                    tma_load_2d(smem_u32(st.b_hi(s)) + st.b_stage / 2, src.blo, kc * KCH, 2 * t0,
+                                bar);
+                } else if (streaming) {
                     mbar_arrive_expect_tx(bar, kAChunkBytes);
                     tma_load_2d(smem_u32(st.a_hi(kc, s)), mhi, kc * KCH, i0, bar);
                     tma_load_2d(smem_u32(st.a_hi(kc, s) + kATileBytes), mlo, kc * KCH, i0, bar);
@@ -448,11 +471,13 @@ __device__ bool tc_tile(TcState& st, const CUtensorMap* mhi, const CUtensorMap* 
             const uint32_t g = g0 + kc, s = g % S, n = g / S;
             if (n > 0) ok = mbar_wait(smem_u32(&bars.empty[s]), (n - 1) & 1, st.status);
             if (!ok) break;
-            if (kc % groups == my_group) {
-                uint8_t* bh = st.b_hi(s);
-                build_B<DAG>(src, V, Nt, t0, ns, N, kc * KCH, scale, bh, bh + st.b_stage / 2,
-                             ptid, nprod);
-                fence_proxy_async();
+            if constexpr (!Src::kTma) {
+                if (kc % groups == my_group) {
+                    uint8_t* bh = st.b_hi(s);
+                    build_B<DAG>(src, V, Nt, t0, ns, N, kc * KCH, scale, bh, bh + st.b_stage / 2,
+                                 ptid, nprod);
+                    fence_proxy_async();
+                }
             }
             __syncwarp();
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
@@ -489,8 +514,10 @@ __device__ bool tc_tile(TcState& st, const CUtensorMap* mhi, const CUtensorMap* 
                     for (int e = 0; e < 8; ++e) {
                         const int tt = (cb >> 1) + e;
                         if (i < V && tt < ns) {
-                            const float wr = fmaf(c[2 * e], kLoInv, m[2 * e]) * inv_scale;
-                            const float wi = fmaf(c[2 * e + 1], kLoInv, m[2 * e + 1]) * inv_scale;
+                            float is = inv_scale;
+                            if constexpr (Src::kTma) is = src.inv[t0 + tt];
+                            const float wr = fmaf(c[2 * e], kLoInv, m[2 * e]) * is;
+                            const float wi = fmaf(c[2 * e + 1], kLoInv, m[2 * e + 1]) * is;
                             epi.store(i, t0 + tt, cur[e], make_float2(wr, wi));
                         }
                     }

@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--chains", type=int, default=256, help="batch workload: chains")
     ap.add_argument("--loop-chains", type=int, default=32,
                     help="batch workload: chains timed as a loop of single-chain launches")
+    ap.add_argument("--loop-chains-fp64", type=int, default=8,
+                    help="batch workload: chains timed as a loop of plain FP64 launches")
     ap.add_argument("--therm", type=int, default=None,
                     help="untimed thermalisation trajectories before warm-up")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -563,6 +565,36 @@ def run_batch(args):
         e.record(stream)
         e.synchronize()
         loop_ms = s.elapsed_time(e)
+    # the plain FP64 GPU path on the first chains, one launch per chain, same
+    # tolerance and fields
+    n64 = min(n, args.loop_chains_fp64)
+    loop64_ms = 0.0
+    if n64 > 0:
+        p64 = [hmc.Params(**{**plist[i].__dict__, "precision": hmc.PREC_FP64,
+                             "team_ctas": 0, "inner_ctas": 0, "tile_slices": 0,
+                             "operand_mode": 0}) for i in range(n64)]
+        ctxs64 = [hmc.Context(p) for p in p64]
+        fields64 = [b.view(phi, i).clone() for i in range(n64)]
+        for i, c in enumerate(ctxs64):
+            c.trajectory(fields64[i], seed, traj, chain=i, allow_not_converged=True)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        for i, c in enumerate(ctxs64):
+            c.trajectory(fields64[i], seed, traj + 1, chain=i, allow_not_converged=True)
+        e.record(stream)
+        e.synchronize()
+        loop64_ms = s.elapsed_time(e)
+    # the mixed loop over exactly those chains
+    loop_mixed_same_ms = 0.0
+    if n64 > 0 and n_loop >= n64:
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        for i, c in enumerate(ctxs[:n64]):
+            c.trajectory(fields[i], seed, traj + 2, chain=i, allow_not_converged=True)
+        e.record(stream)
+        e.synchronize()
+        loop_mixed_same_ms = s.elapsed_time(e)
     sizes = [(p.L, p.Nt) for p in plist]
     flop = sum((applies_per_traj(o, plist[i % n].n_md)) * flops_per_apply(plist[i % n].V,
                                                                          plist[i % n].Nt)
@@ -586,6 +618,11 @@ def run_batch(args):
         "loop_of_single_chain_launches": {
             "chains": n_loop, "ms": loop_ms,
             "trajectories_per_s": n_loop / (loop_ms * 1e-3) if loop_ms else None},
+        "loop_of_single_chain_launches_fp64": {
+            "chains": n64, "ms": loop64_ms,
+            "trajectories_per_s": n64 / (loop64_ms * 1e-3) if loop64_ms else None,
+            "path": "plain FP64 GPU path (hmc_trajectory, precision FP64), same cg_tol",
+            "mixed_same_chains_ms": loop_mixed_same_ms or None},
         "acceptance": statistics.mean(o.accept for o in outs),
         "cg_iterations_per_traj": statistics.mean(o.cg_iterations for o in outs),
         "max_true_residual": max(o.max_true_residual for o in outs),

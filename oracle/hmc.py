@@ -15,7 +15,10 @@ y = M^dag x,  dS/dphi_{x,t} = phi_{x,t}/(delta U) + 2 Im(x_{x,t} conj(y_{x,t})).
 
 Integrator (the paper does not name one): leapfrog
     kick(eps/2) [drift(eps) kick(eps)]^(n-1) drift(eps) kick(eps/2)
-with drift phi += eps*delta*pi and kick pi -= eps*delta*dS/dphi.
+with drift phi += eps*delta*pi and kick pi -= eps*delta*dS/dphi; as an
+option, among the HMC improvements the paper refers to, the second-order
+minimum-norm integrator of Omelyan, Mryglod and Folk (2003) (see
+integrator_schedule).
 CG: plain conjugate gradient on A = M M^dag from x0 = 0, stopping when the
 recursive residual satisfies |r| <= tol |chi|.
 """
@@ -66,26 +69,53 @@ def action(E, phi, chi, delta, U, tol=1e-13, max_iter=10000):
     return bosonic_action(phi, delta, U) + float(np.vdot(chi, x).real)
 
 
-def leapfrog(E, phi, pi, chi, delta, U, eps, n_md, tol=1e-12, max_iter=10000):
-    """Leapfrog of n_md steps.  Returns (phi, pi, x_final, total CG iterations,
-    number of solves).  x_final is the solve at the final phi."""
+# Minimum-norm parameter of the second-order integrator of Omelyan, Mryglod
+# and Folk (Comput. Phys. Commun. 151 (2003) 272), the value that minimises
+# the norm of its leading error terms.
+OMELYAN_LAMBDA = 0.1931833275037836
+
+
+def integrator_schedule(kind, n_md):
+    """(kicks, drift) of a symmetric second-order integrator of n_md steps
+    of length eps: the update is kick(kicks[0] eps), then for m = 1 .. M
+    drift(drift eps) followed by kick(kicks[m] eps).
+      leapfrog:  M = n_md, drift 1, kicks 1/2, 1, ..., 1, 1/2
+      omelyan:   M = 2 n_md, drift 1/2, kicks lam, 1-2lam, 2lam, 1-2lam, ...,
+                 2lam, 1-2lam, lam  (two force evaluations per step)"""
+    if kind == "leapfrog":
+        kicks = [0.5] + [1.0] * (n_md - 1) + [0.5]
+        return kicks, 1.0
+    if kind == "omelyan":
+        lam = OMELYAN_LAMBDA
+        kicks = [lam]
+        for m in range(1, 2 * n_md):
+            kicks.append(1.0 - 2.0 * lam if m % 2 == 1 else 2.0 * lam)
+        kicks.append(lam)
+        return kicks, 0.5
+    raise ValueError(kind)
+
+
+def leapfrog(E, phi, pi, chi, delta, U, eps, n_md, tol=1e-12, max_iter=10000,
+             integrator="leapfrog"):
+    """Molecular dynamics of n_md steps with the given integrator (leapfrog
+    by default, see integrator_schedule).  Returns (phi, pi, x_final, total
+    CG iterations, number of solves).  x_final is the solve at the final phi."""
+    kicks, drift = integrator_schedule(integrator, n_md)
     phi = phi.copy()
     pi = pi.copy()
-    x, it, _ = cg_solve(E, phi, chi, tol, max_iter)
-    iters, solves = it, 1
-    pi = pi - 0.5 * eps * delta * force_from_solution(E, phi, x, delta, U)
-    for step in range(n_md):
-        phi = phi + eps * delta * pi
+    iters, solves = 0, 0
+    for m, k in enumerate(kicks):
+        if m > 0:
+            phi = phi + drift * eps * delta * pi
         x, it, _ = cg_solve(E, phi, chi, tol, max_iter)
         iters += it
         solves += 1
-        kick = eps if step < n_md - 1 else 0.5 * eps
-        pi = pi - kick * delta * force_from_solution(E, phi, x, delta, U)
+        pi = pi - k * eps * delta * force_from_solution(E, phi, x, delta, U)
     return phi, pi, x, iters, solves
 
 
 def trajectory(E, phi0, delta, U, eps, n_md, seed, traj, chain=0,
-               tol=1e-12, max_iter=10000):
+               tol=1e-12, max_iter=10000, integrator="leapfrog"):
     """One HMC update (§2).  Random draws come from the Philox streams.
     Returns a dict with the new field and the diagnostics."""
     Nt, V = phi0.shape
@@ -96,7 +126,7 @@ def trajectory(E, phi0, delta, U, eps, n_md, seed, traj, chain=0,
     H0 = (bosonic_action(phi0, delta, U) + float(np.vdot(rho, rho).real)
           + 0.5 * float(np.sum(pi0 * pi0)))
     phi1, pi1, x1, iters, solves = leapfrog(E, phi0, pi0, chi, delta, U, eps,
-                                            n_md, tol, max_iter)
+                                            n_md, tol, max_iter, integrator)
     H1 = (bosonic_action(phi1, delta, U) + float(np.vdot(chi, x1).real)
           + 0.5 * float(np.sum(pi1 * pi1)))
     dH = H1 - H0

@@ -41,6 +41,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="l6_nt32")
+    ap.add_argument("--integrator", default="leapfrog", choices=["leapfrog", "omelyan"],
+                    help="trajectory mode: molecular-dynamics integrator (the workload's "
+                         "configuration is leapfrog)")
+    ap.add_argument("--n-md", type=int, default=None,
+                    help="trajectory mode: steps per trajectory (default: the workload's)")
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "mixed"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="trajectory", choices=["trajectory", "apply", "brs"],
@@ -172,8 +177,9 @@ def flush_l2(buf, acc):
 def applies_per_traj(out, n_md):
     """M / M^dag applications in one trajectory: chi = M rho, two per CG
     iteration, two per FP64 true-residual check (one per solve and one per
-    reliable update), one M^dag per force."""
-    return 1 + 2 * out.cg_iterations + 2 * (out.cg_solves + out.reliable_updates) + (n_md + 1)
+    reliable update), one M^dag per force (one force per solve, whatever the
+    integrator)."""
+    return 1 + 2 * out.cg_iterations + 2 * (out.cg_solves + out.reliable_updates) + out.cg_solves
 
 
 def measure_dgemm_tflops(torch):
@@ -194,9 +200,9 @@ def measure_dgemm_tflops(torch):
     return 2.0 * n ** 3 / (best * 1e-3) / 1e12
 
 
-def cpu_oracle_rate(name, prec, sample_s, phi_np=None):
+def cpu_oracle_rate(name, prec, sample_s, phi_np=None, integrator="leapfrog", n_md=None):
     """Time the CPU oracle (as it stands) on trajectories of the same workload
-    until about sample_s seconds of work are done."""
+    (and integrator) until about sample_s seconds of work are done."""
     import numpy as np
     from oracle import hmc as ohmc, lattice, operators as ops
     from paper_2210_06874_gb300 import synth
@@ -207,9 +213,11 @@ def cpu_oracle_rate(name, prec, sample_s, phi_np=None):
     t0 = time.perf_counter()
     n = 0
     iters = 0
+    n_md = n_md or w["n_md"]
     while True:
-        out = ohmc.trajectory(E, phi, delta, w["U"], w["traj_length"] / w["n_md"], w["n_md"],
-                              w["seed"], 10_000 + n, 0, tol=w["cg_tol"], max_iter=200000)
+        out = ohmc.trajectory(E, phi, delta, w["U"], w["traj_length"] / n_md, n_md,
+                              w["seed"], 10_000 + n, 0, tol=w["cg_tol"], max_iter=200000,
+                              integrator=integrator)
         phi = out["phi"]
         iters += out["cg_iters"]
         n += 1
@@ -233,7 +241,8 @@ def run_reference(args):
     prec = args.precision or w["precision"]
     rates = []
     for k in range(args.warmup + args.steps):
-        r = cpu_oracle_rate(name, prec, min(args.cpu_sample_s, 20.0))
+        r = cpu_oracle_rate(name, prec, min(args.cpu_sample_s, 20.0),
+                            integrator=args.integrator, n_md=args.n_md)
         if k >= args.warmup:
             rates.append(r["value"])
     value = statistics.mean(rates)
@@ -243,7 +252,7 @@ def run_reference(args):
         "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": name, "precision": "fp64 (oracle)", "L": w["L"], "Nt": w["Nt"],
-                   "n_md": w["n_md"]},
+                   "n_md": args.n_md or w["n_md"], "integrator": args.integrator},
         "cpu_baseline": {"value": value, "unit": "trajectories/s", "cores": os.cpu_count(),
                          "kind": "oracle",
                          "sample": "each step: oracle trajectories of %s for ~%.0f s"
@@ -268,6 +277,9 @@ def run_ours(args):
     build_lib.build()
     name = args.workload
     w, params, prec = workload_params(name, args.precision)
+    if args.n_md is not None:
+        params.n_md = args.n_md
+    params.integrator = 1 if args.integrator == "omelyan" else 0
     tuned = None
     if prec == "mixed" and not args.no_tune:
         from paper_2210_06874_gb300 import autotune
@@ -371,6 +383,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": name, "precision": prec, "L": w["L"], "V": V, "Nt": Nt,
                    "U": w["U"], "beta": w["beta"], "n_md": params.n_md,
+                   "integrator": args.integrator,
                    "cg_tol": params.cg_tol, "thermalisation_trajectories": n_therm,
                    "l2": "flushed (256 MB write + read sweep) between timed trajectories",
                    "parallelism": "replicas (one chain per GPU)",
@@ -378,6 +391,7 @@ def run_ours(args):
         "m_applications_per_s": world * n_app / (ms_per_step * 1e-3),
         "cg_iterations_per_traj": mean_iters,
         "acceptance": statistics.mean(o.accept for o in outs),
+        "mean_abs_dH": statistics.mean(abs(o.dH) for o in outs),
         "max_true_residual": max(o.max_true_residual for o in outs),
         "e2e": {"value": world / (e2e_ms * 1e-3), "unit": "trajectories/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -388,7 +402,8 @@ def run_ours(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_rate(name, prec, args.cpu_sample_s,
-                                               phi_np=phi.cpu().numpy())
+                                               phi_np=phi.cpu().numpy(),
+                                               integrator=args.integrator, n_md=params.n_md)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -110,6 +110,12 @@ typedef struct hmc_params {
                             2 never.  Resident E accepts inner_ctas as a
                             multiple of the 128-site blocks: the extra CTAs
                             take further slice tiles of the same block. */
+    int integrator;      /* molecular dynamics of hmc_trajectory: 0 leapfrog
+                            (n_md steps, n_md + 1 force evaluations), 1 the
+                            second-order minimum-norm integrator of Omelyan,
+                            Mryglod and Folk (2003), lambda = 0.19318...
+                            (n_md steps, 2 n_md + 1 force evaluations, a
+                            much smaller energy violation at equal step) */
 } hmc_params;
 
 typedef struct hmc_cg_stats {

@@ -142,6 +142,7 @@ static int valid_params(const hmc_params* p) {
     if (p->inner_ctas < 0 || p->inner_ctas > 1024) return 0;
     if (p->operand_mode < 0 || p->operand_mode > 3) return 0;
     if (p->cluster_mode < 0 || p->cluster_mode > 2) return 0;
+    if (p->integrator < 0 || p->integrator > 1) return 0;
     if (p->tile_slices != 0 && p->tile_slices != 8 && p->tile_slices != 16 &&
         p->tile_slices != 32)
         return 0;
@@ -338,6 +339,7 @@ int hmc_trajectory(hmc_ctx* c, double* phi, uint64_t seed, uint64_t traj_index, 
     a.tol = c->params.cg_tol;
     a.max_iter = c->params.cg_max_iter;
     a.ru_delta = c->params.ru_delta;
+    a.integrator = c->params.integrator;
     int st;
     if (c->params.precision == HMC_PREC_FP64)
         st = launch_trajectory_f64(c->view, c->num_sms, a, s);

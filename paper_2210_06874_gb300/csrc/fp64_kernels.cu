@@ -131,10 +131,12 @@ __global__ void __launch_bounds__(NTHR) k_trajectory(ChainView c, TrajArgs a) {
     ea.pi = c.pi;
     ea.inv_dU = inv_dU;
     const double ed = a.eps * c.delta;
-    for (int step = 0; step <= a.n_md; ++step) {
+    const double edrift = md_drift(a) * ed;
+    const int n_stages = md_stages(a);
+    for (int step = 0; step <= n_stages; ++step) {
         if (step > 0) {
             HMC_TEAM_ELEMS(e, c, tm) {
-                const double ph = fma(ed, c.pi[e], phi[e]);
+                const double ph = fma(edrift, c.pi[e], phi[e]);
                 phi[e] = ph;
                 double s, co;
                 sincos(ph, &s, &co);
@@ -148,7 +150,7 @@ __global__ void __launch_bounds__(NTHR) k_trajectory(ChainView c, TrajArgs a) {
         ++solves;
         max_res = fmax(max_res, res.true_res);
         if (res.status != HMC_OK && status == HMC_OK) status = res.status;
-        ea.kick = ((step == 0 || step == a.n_md) ? 0.5 : 1.0) * ed;
+        ea.kick = md_kick(a, step) * ed;
         apply_team<true, EPI_FORCE>(c, tm, c.x, nullptr, ea, sm);
         if (!team_barrier(tm)) return;
     }

@@ -18,7 +18,31 @@ struct TrajArgs {
     double tol;
     int max_iter;
     double ru_delta;    // mixed path: reliable-update trigger
+    int integrator;     // 0 leapfrog, 1 second-order minimum-norm (Omelyan)
 };
+
+// Molecular-dynamics schedule of a symmetric second-order integrator: kick
+// md_kick(0) eps, then for m = 1 .. md_stages: drift md_drift eps, kick
+// md_kick(m) eps (one force evaluation per kick).
+//   leapfrog:  n_md stages, drift 1, kicks 1/2, 1, ..., 1, 1/2
+//   minimum-norm (Omelyan, Mryglod, Folk 2003): 2 n_md stages, drift 1/2,
+//   kicks lam, 1-2lam, 2lam, 1-2lam, ..., 2lam, 1-2lam, lam with
+//   lam = 0.1931833275037836 (the minimum of the norm of its error terms)
+constexpr double kOmelyanLambda = 0.1931833275037836;
+__host__ __device__ inline int md_stages(const TrajArgs& a) {
+    return a.integrator == 1 ? 2 * a.n_md : a.n_md;
+}
+__host__ __device__ inline double md_drift(const TrajArgs& a) {
+    return a.integrator == 1 ? 0.5 : 1.0;
+}
+__host__ __device__ inline double md_kick(const TrajArgs& a, int m) {
+    const int M = md_stages(a);
+    if (a.integrator == 1) {
+        if (m == 0 || m == M) return kOmelyanLambda;
+        return (m & 1) ? 1.0 - 2.0 * kOmelyanLambda : 2.0 * kOmelyanLambda;
+    }
+    return (m == 0 || m == M) ? 0.5 : 1.0;
+}
 
 // Slots of ChainView::scalars written by the trajectory kernels.
 enum TrajSlot : int {

@@ -693,10 +693,12 @@ __device__ bool run_trajectory(const ChainView& c, Team& tm, TcState& st, f64::S
     ea.pi = c.pi;
     ea.inv_dU = inv_dU;
     const double ed = a.eps * c.delta;
-    for (int step = 0; ok && step <= a.n_md; ++step) {
+    const double edrift = md_drift(a) * ed;
+    const int n_stages = md_stages(a);
+    for (int step = 0; ok && step <= n_stages; ++step) {
         if (step > 0) {
             HMC_TEAM_ELEMS(e, c, tm) {
-                const double ph = fma(ed, c.pi[e], phi[e]);
+                const double ph = fma(edrift, c.pi[e], phi[e]);
                 phi[e] = ph;
                 double s, co;
                 sincos(ph, &s, &co);
@@ -712,7 +714,7 @@ __device__ bool run_trajectory(const ChainView& c, Team& tm, TcState& st, f64::S
         ++solves;
         max_res = fmax(max_res, res.true_res);
         if (res.status != HMC_OK && status == HMC_OK) status = res.status;
-        ea.kick = ((step == 0 || step == a.n_md) ? 0.5 : 1.0) * ed;
+        ea.kick = md_kick(a, step) * ed;
         f64::apply_team<true, f64::EPI_FORCE>(c, tm, c.x, nullptr, ea, sm64);
         ok = team_barrier(tm);
     }
@@ -1258,6 +1260,7 @@ int tc_batch_create(const hmc_params* p, int n, TcBatch** out) {
         std::memset(&it.a, 0, sizeof(it.a));
         it.a.chain = (uint32_t)i;
         it.a.n_md = c->params.n_md;
+        it.a.integrator = c->params.integrator;
         it.a.eps = c->params.traj_length / c->params.n_md;
         it.a.tol = c->params.cg_tol;
         it.a.max_iter = c->params.cg_max_iter;

@@ -48,7 +48,8 @@ class hmc_params(ctypes.Structure):
                 ("cg_max_iter", ctypes.c_int), ("precision", ctypes.c_int),
                 ("ru_delta", ctypes.c_double), ("team_ctas", ctypes.c_int),
                 ("tile_slices", ctypes.c_int), ("inner_ctas", ctypes.c_int),
-                ("operand_mode", ctypes.c_int), ("cluster_mode", ctypes.c_int)]
+                ("operand_mode", ctypes.c_int), ("cluster_mode", ctypes.c_int),
+                ("integrator", ctypes.c_int)]
 
 
 class hmc_cg_stats(ctypes.Structure):
@@ -147,6 +148,7 @@ class Params:
     inner_ctas: int = 0
     operand_mode: int = 0
     cluster_mode: int = 0
+    integrator: int = 0
 
     @property
     def V(self):
@@ -160,7 +162,8 @@ class Params:
         return hmc_params(self.L, self.Nt, self.kappa, self.U, self.beta, self.n_md,
                           self.traj_length, self.cg_tol, self.cg_max_iter, self.precision,
                           self.ru_delta, self.team_ctas, self.tile_slices,
-                          self.inner_ctas, self.operand_mode, self.cluster_mode)
+                          self.inner_ctas, self.operand_mode, self.cluster_mode,
+                          self.integrator)
 
 
 class Context:

@@ -52,7 +52,8 @@ def bad(**kw):
                                          ("n_md", 0), ("cg_tol", 0.0), ("cg_max_iter", 0),
                                          ("precision", 7), ("ru_delta", 1.5),
                                          ("L", 30000), ("operand_mode", 4),
-                                         ("cluster_mode", 3), ("cluster_mode", -1)])
+                                         ("cluster_mode", 3), ("cluster_mode", -1),
+                                         ("integrator", 2), ("integrator", -1)])
 def test_ctx_create_rejects_bad_params(lib, field, value):
     h = ctypes.c_void_p()
     p = bad(**{field: value})

@@ -230,6 +230,38 @@ def cpu_oracle_rate(name, prec, sample_s, phi_np=None, integrator="leapfrog", n_
                       "BLAS threads as configured" % (n, name, iters, dt)}
 
 
+def cpu_oracle_rate_single_thread(name, prec, sample_s, phi_np=None, integrator="leapfrog",
+                                  n_md=None):
+    """The same oracle timing in a child process with BLAS and OpenMP pinned
+    to one thread (thread counts are fixed when NumPy loads its BLAS); the
+    start field goes through a temporary .npy file."""
+    import tempfile
+    import numpy as np
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+               MKL_NUM_THREADS="1", BLIS_NUM_THREADS="1")
+    fd, path = tempfile.mkstemp(suffix=".npy")
+    os.close(fd)
+    if phi_np is not None:
+        np.save(path, phi_np)
+    code = ("import json, sys, numpy as np; sys.path.insert(0, %r); import bench; "
+            "phi = np.load(%r) if %r else None; "
+            "print(json.dumps(bench.cpu_oracle_rate(%r, %r, %r, phi_np=phi, integrator=%r, "
+            "n_md=%r)))"
+            % (os.path.dirname(os.path.abspath(__file__)), path, phi_np is not None, name, prec,
+               sample_s, integrator, n_md))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True,
+                           text=True, timeout=sample_s * 10 + 120)
+        out = json.loads(r.stdout.strip().splitlines()[-1])
+        out["cores"] = 1
+        out["sample"] = out["sample"].replace("BLAS threads as configured", "one thread")
+        return out
+    except Exception as e:   # a reporting extra: never fail the bench on it
+        return {"unavailable": str(e)[:200]}
+    finally:
+        os.unlink(path)
+
+
 # ----------------------------------------------------------------- reference arm
 def run_reference(args):
     rank, _, world = dist_env()
@@ -404,6 +436,9 @@ def run_ours(args):
         line["cpu_baseline"] = cpu_oracle_rate(name, prec, args.cpu_sample_s,
                                                phi_np=phi.cpu().numpy(),
                                                integrator=args.integrator, n_md=params.n_md)
+        line["cpu_baseline"]["single_thread"] = cpu_oracle_rate_single_thread(
+            name, prec, min(args.cpu_sample_s, 10.0), phi_np=phi.cpu().numpy(),
+            integrator=args.integrator, n_md=params.n_md)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -155,15 +155,30 @@ __device__ __forceinline__ void tile_coords(int tile, int nti, int ns_tile, int 
 template <bool DAG, class Src, class Epi>
 __device__ bool apply_team(const ChainView& c, const Team& tm, TcState& st,
                            const CUtensorMap* mhi, const CUtensorMap* mlo, int ns_tile,
-                           const Src& src, float scale, float inv, Epi& epi) {
+                           const Src& src, float scale, float inv, Epi& epi,
+                           bool res_b = false) {
     const int nti = c.Vr / TM, ntt = (c.Nt + ns_tile - 1) / ns_tile;
     // tiles are dealt round robin over the team; in resident mode the team
     // size is a multiple of the site blocks, so a CTA only meets tiles of
-    // its own site block (rank mod nti), whose rows of E it holds
-    for (int tile = tm.rank; tile < nti * ntt; tile += tm.size) {
-        int i0, t0, ns;
-        tile_coords(tile, nti, ns_tile, c.Nt, i0, t0, ns);
-        if (!tc_tile<DAG>(st, mhi, mlo, c.V, c.Nt, c.Vp, i0, t0, ns, src, scale, inv, epi))
+    // its own site block (rank mod nti), whose rows of E it holds.  With a
+    // resident B, slice tiles go round robin and a CTA runs all site blocks
+    // of each of its slice tiles, building that B once.  One call site of
+    // the tile keeps it inlined once.
+    for (int j = 0;; ++j) {
+        int i0, t0, ns, rflag = 0;
+        if (res_b) {
+            const int stl = tm.rank + (j / nti) * tm.size, rb = j % nti;
+            if (stl >= ntt) break;
+            i0 = rb * TM;
+            t0 = stl * ns_tile;
+            ns = min(ns_tile, c.Nt - t0);
+            rflag = rb == 0 ? 1 : 2;
+        } else {
+            const int tile = tm.rank + j * tm.size;
+            if (tile >= nti * ntt) break;
+            tile_coords(tile, nti, ns_tile, c.Nt, i0, t0, ns);
+        }
+        if (!tc_tile<DAG>(st, mhi, mlo, c.V, c.Nt, c.Vp, i0, t0, ns, src, scale, inv, epi, rflag))
             return false;
     }
     return true;
@@ -265,6 +280,7 @@ struct PersistentArgs {
     int ns_tile;
     int inner;         // CTAs of the FP32 inner loop
     int cluster;       // > 1: launched in clusters of this size, the inner team is cluster 0
+    int res_b;         // streaming layout: resident B per slice tile (apply_team)
     int mode;          // OperandMode: resident needs inner a multiple of the site blocks
     int vec_resident;  // resident mode with one CTA: FP32 CG vectors in shared memory
     double tol;
@@ -510,7 +526,7 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
                 SrcDirection dir{rf, c.r, pf, s_cg.beta, refresh, c.V};
                 EpiDirection ed{dir, pn, rf, qf, cisf, c.Nt, 0.f};
                 if (!apply_team<true>(c, ti, st, mhi, mlo, pa.ns_tile, dir, s_cg.sc, s_cg.inv,
-                                      ed))
+                                      ed, pa.res_b != 0))
                     return false;
                 float qq;
                 if (!team_sum_f(ti, ed.acc, qq)) return false;
@@ -525,7 +541,7 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
                 SrcPhase srcq{qf, cisf, c.V};
                 EpiCgUpdate eu{qf, pf, xf, rf, s_cg.alpha, c.V, 0.f};
                 if (!apply_team<false>(c, ti, st, mhi, mlo, pa.ns_tile, srcq, s_cg.sc, s_cg.inv,
-                                       eu))
+                                       eu, pa.res_b != 0))
                     return false;
                 float rr_new;
                 if (!team_sum_f(ti, eu.acc, rr_new)) return false;
@@ -1000,6 +1016,17 @@ static int team_size(hmc_ctx* c, const void* kernel) {
     return std::max(1, std::min(g, want));
 }
 
+// Resident B per slice tile pays when a CTA runs several site blocks of the
+// same slices: streaming layout, at least two site blocks, every CTA of the
+// inner team with a slice tile, and the tile's B within the area after the
+// E ring.
+static bool res_b_ok(const ChainView& v, int mode, int ns, int inner) {
+    const int nti = v.Vr / tc::TM, ntt = (v.Nt + ns - 1) / ns;
+    const int N = ((2 * ns + 15) / 16) * 16;
+    return mode == tc::kStreaming && nti >= 2 && inner <= ntt &&
+           tc::res_b_bytes(N, v.Vp) <= tc::kResBArea;
+}
+
 // Cluster size of the small-lattice CUDA-core mode: inner_ctas when given,
 // else the largest of 8, 4, 2, 1 that fits (each CTA at least 2 slices).
 static int small_cluster(const hmc_ctx* c) {
@@ -1024,6 +1051,7 @@ static tc::PersistentArgs persistent_args(hmc_ctx* c, int grid, double tol, int 
         pa.max_iter = max_iter;
         pa.ru_delta = c->params.ru_delta;
         pa.cluster = 0;
+        pa.res_b = 0;
         return pa;
     }
     // inner team: one CTA while the whole lattice fits in a handful of tiles
@@ -1060,6 +1088,7 @@ static tc::PersistentArgs persistent_args(hmc_ctx* c, int grid, double tol, int 
     pa.max_iter = max_iter;
     pa.ru_delta = c->params.ru_delta;
     pa.cluster = 0;
+    pa.res_b = res_b_ok(v, pa.mode, pa.ns_tile, pa.inner) ? 1 : 0;
     return pa;
 }
 
@@ -1253,6 +1282,7 @@ int tc_batch_create(const hmc_params* p, int n, TcBatch** out) {
                 it.pa.mode = tc::kSmall;
                 it.pa.vec_resident = 0;
             }
+            it.pa.res_b = res_b_ok(it.v, it.pa.mode, it.pa.ns_tile, 1) ? 1 : 0;
         }
         it.pa.tol = c->params.cg_tol;
         it.pa.max_iter = c->params.cg_max_iter;

@@ -248,6 +248,14 @@ __device__ __forceinline__ void build_B(const Src& src, int V, int Nt, int t0, i
     }
 }
 
+// Resident B (tile argument res_b != 0, streaming layout): the B operand of
+// all K chunks of a slice tile, hi chunks then lo chunks of N x 128 bytes,
+// in the area after the E ring.
+__host__ __device__ constexpr size_t res_b_bytes(int N, int Vp) {
+    return 2 * (size_t)(Vp / KCH) * (size_t)N * 128;
+}
+constexpr size_t kResBArea = kOperandBytes - (size_t)kMaxStages * kAChunkBytes;
+
 // Per-CTA state of the tensor-core tile pipeline (set up once per launch).
 struct TcState {
     uint8_t* base;     // 1024-aligned operand area
@@ -389,10 +397,16 @@ __device__ __forceinline__ void vector_scale_f(float n2, float& scale, float& in
 // (t, i) needs, Epi::store(i, t, in, w) receives w = (E u)_i for the tile's
 // source slice of target t (unscaled; before shift sign and phase).
 // Returns false if a bounded wait failed (status set).  All threads call it.
+// res_b (streaming layout only): 0 builds B chunk by chunk in the ring;
+// 1 first builds the B of all K chunks of slices t0..t0+ns-1 into the
+// resident area with all threads, 2 reuses the resident B of the previous
+// tile (same slices, another site block).  The epilogue runs on all eight
+// warps once the roles are done (warps 4..7 the first half of the 16-column
+// blocks, warps 0..3 the rest; a warp reads its TMEM lane quarter).
 template <bool DAG, class Src, class Epi>
 __device__ bool tc_tile(TcState& st, const CUtensorMap* mhi, const CUtensorMap* mlo, int V,
                         int Nt, int Vp, int i0, int t0, int ns, const Src& src, float scale,
-                        float inv_scale, Epi& epi) {
+                        float inv_scale, Epi& epi, int res_b = 0) {
     TileBars& bars = *st.bars;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = Vp / KCH;
@@ -401,6 +415,50 @@ __device__ bool tc_tile(TcState& st, const CUtensorMap* mhi, const CUtensorMap* 
     const bool streaming = st.mode == kStreaming;
     const uint32_t g0 = st.gchunk;
     bool ok = true;
+    const uint32_t chunk_b = (uint32_t)N * 128u;
+    uint8_t* bres = st.base + st.b_off;
+    if constexpr (!Src::kTma) {
+        if (res_b == 1) {
+            // all chunks of the tile's B at once: rows 2j (re), 2j+1 (im),
+            // zero for slices >= ns and sites >= V
+            const int nkb = Vp / 8;
+            for (int w = threadIdx.x; w < (N / 2) * nkb; w += blockDim.x) {
+                const int j = w / nkb, kbi = w - j * nkb, kb = kbi * 8;
+                const int kc = kb / KCH, grp = kbi & 7;
+                float2 v8[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v8[e] = make_float2(0.f, 0.f);
+                if (j < ns && kb < V) {
+                    const int ts = source_slice<DAG>(t0 + j, Nt);
+                    if (kb + 8 <= V) {
+                        src.load8(ts, kb, v8);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e)
+                            if (kb + e < V) v8[e] = src.load1(ts, kb + e);
+                    }
+                }
+                float re[8], im[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    re[e] = v8[e].x * scale;
+                    im[e] = v8[e].y * scale;
+                }
+                uint4 hr, lr, hm, lm;
+                split8(re, hr, lr);
+                split8(im, hm, lm);
+                const int jr = 2 * j, ji = jr + 1;
+                uint8_t* bh = bres + (size_t)kc * chunk_b;
+                uint8_t* bl = bh + (size_t)nk * chunk_b;
+                *reinterpret_cast<uint4*>(bh + jr * 128 + ((grp ^ (jr & 7)) << 4)) = hr;
+                *reinterpret_cast<uint4*>(bl + jr * 128 + ((grp ^ (jr & 7)) << 4)) = lr;
+                *reinterpret_cast<uint4*>(bh + ji * 128 + ((grp ^ (ji & 7)) << 4)) = hm;
+                *reinterpret_cast<uint4*>(bl + ji * 128 + ((grp ^ (ji & 7)) << 4)) = lm;
+            }
+            fence_proxy_async();
+            __syncthreads();
+        }
+    }
 
     if (warp == kWarpTma) {
         if (lane == 0) {
@@ -437,7 +495,11 @@ __device__ bool tc_tile(TcState& st, const CUtensorMap* mhi, const CUtensorMap* 
                 if (!ok) break;
                 fence_after_sync();
                 const uint32_t ah = smem_u32(st.a_hi(kc, s)), al = ah + kATileBytes;
-                const uint32_t bh = smem_u32(st.b_hi(s)), bl = bh + st.b_stage / 2;
+                uint32_t bh = smem_u32(st.b_hi(s)), bl = bh + st.b_stage / 2;
+                if (res_b != 0) {
+                    bh = smem_u32(bres + (size_t)kc * chunk_b);
+                    bl = bh + (uint32_t)nk * chunk_b;
+                }
 #pragma unroll
                 for (int kk = 0; kk < KCH / 16; ++kk) {
                     const uint32_t off = kk * 32;
@@ -472,7 +534,7 @@ __device__ bool tc_tile(TcState& st, const CUtensorMap* mhi, const CUtensorMap* 
             if (n > 0) ok = mbar_wait(smem_u32(&bars.empty[s]), (n - 1) & 1, st.status);
             if (!ok) break;
             if constexpr (!Src::kTma) {
-                if (kc % groups == my_group) {
+                if (res_b == 0 && kc % groups == my_group) {
                     uint8_t* bh = st.b_hi(s);
                     build_B<DAG>(src, V, Nt, t0, ns, N, kc * KCH, scale, bh, bh + st.b_stage / 2,
                                  ptid, nprod);
@@ -484,29 +546,36 @@ __device__ bool tc_tile(TcState& st, const CUtensorMap* mhi, const CUtensorMap* 
                                             smem_u32(&bars.full[s]))
                                         : "memory");
         }
-        // epilogue on warps 4..7: lane quarter (warp % 4) of TMEM, all columns.
-        // The inputs of a block of 8 slices are fetched together (the first
-        // block before the accumulator is ready, overlapping the MMA tail).
-        if (warp >= kFirstEpiWarp) {
-            using In = typename Epi::In;
-            const int row = (warp & 3) * 32 + lane;
-            const int i = i0 + row;
-            In cur[8];
-            auto fetch = [&](int cb, In (&dst)[8]) {
+    }
+    // epilogue on all warps: lane quarter (warp % 4) of TMEM, 16-column
+    // blocks [b0, b1).  The inputs of a block of 8 slices are fetched
+    // together (the first block before the accumulator is ready, overlapping
+    // the MMA tail).
+    __syncwarp();
+    {
+        const int nb = N / 16, half = (nb + 1) / 2;
+        const bool hi_warps = warp >= kFirstEpiWarp;
+        const int b0 = hi_warps ? 0 : half, b1 = hi_warps ? half : nb;
+        using In = typename Epi::In;
+        const int row = (warp & 3) * 32 + lane;
+        const int i = i0 + row;
+        In cur[8];
+        auto fetch = [&](int cb, In (&dst)[8]) {
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int tt = (cb >> 1) + e;
-                    if (i < V && tt < ns) dst[e] = epi.load(i, t0 + tt);
-                }
-            };
-            if (ok) fetch(0, cur);
+            for (int e = 0; e < 8; ++e) {
+                const int tt = (cb >> 1) + e;
+                if (i < V && tt < ns) dst[e] = epi.load(i, t0 + tt);
+            }
+        };
+        if (b0 < b1) {
+            if (ok) fetch(b0 * 16, cur);
             if (ok) ok = mbar_wait(smem_u32(&bars.acc_full), st.ntile & 1, st.status);
             fence_after_sync();
             ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld below is warp-collective
             if (ok) {
                 const uint32_t tl = bars.tmem_base + ((uint32_t)((warp & 3) * 32) << 16);
-                for (int cb = 0; cb < N; cb += 16) {
-                    if (cb > 0) fetch(cb, cur);
+                for (int cb = b0 * 16; cb < b1 * 16; cb += 16) {
+                    if (cb > b0 * 16) fetch(cb, cur);
                     float m[16], c[16];
                     tmem_ld16(tl + cb, m);
                     tmem_ld16(tl + kCorrCol + cb, c);

@@ -82,7 +82,7 @@ typedef struct hmc_params {
                             since the last update (0 selects the default) */
     int team_ctas;       /* CTAs of a persistent launch (0: automatic) */
     int tile_slices;     /* time slices per tensor-core tile, one of 8, 16, 32
-                            (0: automatic) */
+                            (operand_mode 4: 1..64; 0: automatic) */
     int inner_ctas;      /* CTAs running the FP32 iterations of the mixed CG
                             (0: automatic; the FP64 steps use all CTAs) */
     int operand_mode;    /* mixed path: 0 automatic, 1 stream E through shared
@@ -100,7 +100,11 @@ typedef struct hmc_params {
                             memory of a CTA (about V <= 128 at 8 slices);
                             HMC_ERR_UNSUPPORTED otherwise, or if the device
                             refuses the cluster (sizes above 8 are
-                            non-portable) */
+                            non-portable), 4 slice-major tensor-core tiles:
+                            up to 64 time slices (x re/im) as the MMA's
+                            M = 128 and up to 288 sites as its N, E
+                            streamed, one FP32 accumulator of a scaled
+                            FP16 split (any V) */
     int cluster_mode;    /* mixed path, inner team of 2..8 CTAs: 0 automatic
                             (launch it as one thread-block cluster, whose
                             barriers and sums go through distributed shared

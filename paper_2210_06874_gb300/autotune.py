@@ -4,8 +4,9 @@ For one chain it times short mixed CG solves with a fixed iteration count
 (max_iter iterations, convergence not required: the per-iteration cost does
 not depend on the residual) for candidate shapes -- CTAs of the persistent
 launch (team_ctas), CTAs of the FP32 inner loop (inner_ctas), time slices per
-tensor-core tile (tile_slices), streamed or resident E (operand_mode) -- and
-keeps the fastest.  Timing uses CUDA
+tensor-core tile (tile_slices), streamed or resident E, site-major or
+slice-major tiles, CUDA-core cluster mode (operand_mode) -- and keeps the
+fastest.  Timing uses CUDA
 events on the current stream around calls through the C ABI; results are
 cached per (L, Nt, team constraint) for the process.
 """
@@ -21,7 +22,7 @@ _cache = {}
 def small_feasible(V, Nt, C):
     """Host copy of the feasibility rule of the CUDA-core cluster mode
     (operand_mode 3): 1 <= C <= 16 CTAs, each with 1..16 time slices, and the
-    shared-memory layout within the 204 KB operand area."""
+    shared-memory layout within the 208 KB operand area."""
     if C < 1 or C > 16 or Nt < C or -(-Nt // C) > 16:
         return False
     S = -(-Nt // C)
@@ -32,16 +33,18 @@ def small_feasible(V, Nt, C):
     r16 = lambda b: (b + 15) // 16 * 16
     total = (r16(V * Vr * 4) + 6 * r16(S * V * 8) + 2 * r16(V * SP * 8) + 2 * r16(V * 8) +
              r16(KS * S * Vr * 8))
-    return total <= 204 * 1024
+    return total <= 208 * 1024
 
 
 def candidates(params, num_sms, single_cta=False):
     """Shapes (team_ctas, inner_ctas, tile_slices, operand_mode) worth timing:
     streamed E with one CTA or teams sized to the tensor-core / FP64 tile
-    counts, resident E (one CTA per 128-site block) where E fits, and the
-    CUDA-core cluster mode (clusters of 1, 2, 4, 8 or 16 CTAs) where it fits;
-    16 is a non-portable cluster size that a device may refuse (the tuner
-    then skips it)."""
+    counts, resident E (one CTA per 128-site block) where E fits, the
+    CUDA-core cluster mode (clusters of 1, 2, 4, 8 or 16 CTAs) where it fits
+    (16 is a non-portable cluster size that a device may refuse; the tuner
+    then skips it), and slice-major tiles (operand_mode 4, slices per tile
+    chosen by the library: tile_slices 0) on one CTA or inner teams of 2, 4
+    and 8 CTAs."""
     V, Nt = params.V, params.Nt
     nti = (V + 127) // 128
     vp = ((V + 63) // 64) * 64
@@ -66,6 +69,11 @@ def candidates(params, num_sms, single_cta=False):
                 out.append((team, inner, ns, 1))
         if vp <= 256 and nti <= num_sms and ns <= 16:
             out.append((max(nti, min(f64_tiles, num_sms)), nti, ns, 2))
+    if single_cta:
+        out.append((1, 1, 0, 4))
+    else:
+        for inner in (1, 2, 4, 8):
+            out.append((max(inner, min(f64_tiles, num_sms)), inner, 0, 4))
     return sorted(set(out))
 
 

@@ -140,12 +140,15 @@ static int valid_params(const hmc_params* p) {
     if (p->ru_delta < 0.0 || p->ru_delta >= 1.0) return 0;
     if (p->team_ctas < 0 || p->team_ctas > 1024) return 0;
     if (p->inner_ctas < 0 || p->inner_ctas > 1024) return 0;
-    if (p->operand_mode < 0 || p->operand_mode > 3) return 0;
+    if (p->operand_mode < 0 || p->operand_mode > 4) return 0;
     if (p->cluster_mode < 0 || p->cluster_mode > 2) return 0;
     if (p->integrator < 0 || p->integrator > 1) return 0;
-    if (p->tile_slices != 0 && p->tile_slices != 8 && p->tile_slices != 16 &&
-        p->tile_slices != 32)
+    if (p->operand_mode == 4) {
+        if (p->tile_slices < 0 || p->tile_slices > 64) return 0;
+    } else if (p->tile_slices != 0 && p->tile_slices != 8 && p->tile_slices != 16 &&
+               p->tile_slices != 32) {
         return 0;
+    }
     // indices of [Nt][V] vectors are 32-bit in the kernels
     const long long N = 2LL * p->L * p->L * (long long)p->Nt;
     if (N > (1LL << 30)) return 0;

@@ -19,6 +19,11 @@ struct ChainView {
     const void* E_hi;           // __half [Vr][Vp]
     const void* E_lo;           // __half [Vr][Vp]
     int Vr, Vp;                 // padded rows (multiple of 128), cols (multiple of 64)
+    // scaled FP16 split of the slice-major tensor-core tile:
+    //   2^eE E ~= Ew_hi + Ew_lo (plain remainder), same padding; e_inv = 2^-eE
+    const void* Ew_hi;          // __half [Vr][Vp]
+    const void* Ew_lo;          // __half [Vr][Vp]
+    float e_inv;
     // FP64 workspaces, double2 [Nt][V] each
     double2 *cis;               // exp(i phi)
     double2 *x, *r, *p, *q, *chi, *rho;

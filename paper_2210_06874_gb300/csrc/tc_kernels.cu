@@ -13,6 +13,7 @@
 #include "fp64_path.cuh"
 #include "tc_path.h"
 #include "tc_tile.cuh"
+#include "tc_wide.cuh"
 #include "small_cg.cuh"
 
 namespace hmc {
@@ -29,7 +30,22 @@ struct TcCtx {
     __half* blo;
     float* inv_col;
     int b_rows;
+    // slice-major tiles (operand_mode 4): maps of the scaled split of E (box
+    // rows = W / nmma), sites per tile of the solver and of standalone
+    // applications, slices per standalone tile, and the maps of the
+    // pre-split U (plain remainder) over bhi / blo with 128-row boxes
+    CUtensorMap map_whi, map_wlo, map_uhi, map_ulo;
+    int w_cg, w_apply, ns_wapply;
 };
+
+namespace tc {
+// TMA box rows of the pre-split U for tiles of ns slices: 2 ns rounded up
+// to 16 (the swizzle atom is 8 rows; whole 1024-byte atoms), at most 128.
+__host__ __device__ inline int wide_u_rows(int ns) {
+    const int r = ((2 * ns + 15) / 16) * 16;
+    return r > 128 ? 128 : r;
+}
+}  // namespace tc
 
 namespace tc {
 
@@ -184,15 +200,34 @@ __device__ bool apply_team(const ChainView& c, const Team& tm, TcState& st,
     return true;
 }
 
+// All slice-major tiles of one application (W sites x ns_tile slices each),
+// dealt round robin over the team.
+template <bool DAG, class Src, class Epi>
+__device__ bool apply_team_w(const ChainView& c, const Team& tm, TcState& st, int W,
+                             const CUtensorMap* mhi, const CUtensorMap* mlo, int ns_tile,
+                             const Src& src, float scale, float inv, Epi& epi) {
+    const WideGeom g = wide_geom(W);
+    const int nsi = (c.V + W - 1) / W, ntt = (c.Nt + ns_tile - 1) / ns_tile;
+    for (int tile = tm.rank; tile < nsi * ntt; tile += tm.size) {
+        const int i0 = (tile % nsi) * W, t0 = (tile / nsi) * ns_tile;
+        const int ns = min(ns_tile, c.Nt - t0);
+        if (!tc_wtile<DAG>(st, g, mhi, mlo, c.V, c.Nt, c.Vp, i0, t0, ns, src, scale, inv,
+                           c.e_inv, epi))
+            return false;
+    }
+    return true;
+}
+
 // ---------------------------------------------------------------- standalone
 // B operand of one standalone application, split before the tiles run: for
 // target slice t (one block) the source u = in_{t+1} (M^dag) or
 // e^{i phi_{t-1}} in_{t-1} (M), scaled by 2^e with max |Re u|, |Im u| in
 // [2^14, 2^15), written as FP16 hi = fp16(s u) and lo = fp16((s u - hi) 2^11)
-// in rows 2t (re) and 2t+1 (im), zero from V to Vp; inv[t] = 2^-e.  Also
-// writes the FP32 phase table of slice t (the M^dag epilogue reads it).
+// (PLAIN, for the slice-major tile: lo = fp16(s u - hi)) in rows 2t (re) and
+// 2t+1 (im), zero from V to Vp; inv[t] = 2^-e.  Also writes the FP32 phase
+// table of slice t (the M^dag epilogue reads it).
 // Dynamic shared memory: V float2 (the source slice).
-template <bool DAG>
+template <bool DAG, bool PLAIN>
 __global__ void __launch_bounds__(256)
     k_split(const double* __restrict__ phi, const float2* __restrict__ in,
             float2* __restrict__ cis_f, __half* __restrict__ bhi, __half* __restrict__ blo,
@@ -239,8 +274,9 @@ __global__ void __launch_bounds__(256)
             const float x = u.x * sc, y = u.y * sc;
             h0 = __float2half_rn(x);
             h1 = __float2half_rn(y);
-            l0 = __float2half_rn((x - __half2float(h0)) * kLoScale);
-            l1 = __float2half_rn((y - __half2float(h1)) * kLoScale);
+            const float ls = PLAIN ? 1.f : kLoScale;
+            l0 = __float2half_rn((x - __half2float(h0)) * ls);
+            l1 = __float2half_rn((y - __half2float(h1)) * ls);
         }
         hr[k] = h0;
         hr[Vp + k] = h1;
@@ -268,6 +304,26 @@ __global__ void __launch_bounds__(NTHR, 1)
     tc_teardown(st);
 }
 
+// Standalone application on slice-major tiles: W sites x ns_tile slices per
+// CTA; E' and the pre-split U arrive by TMA.
+template <bool DAG>
+__global__ void __launch_bounds__(NTHR, 1)
+    k_apply_w(const __grid_constant__ CUtensorMap mhi, const __grid_constant__ CUtensorMap mlo,
+              const __grid_constant__ CUtensorMap uhi, const __grid_constant__ CUtensorMap ulo,
+              ChainView c, int W, int ns_tile, const float2* in, float2* out, const float* inv) {
+    extern __shared__ __align__(1024) uint8_t dyn[];
+    TcState st;
+    tc_setup(st, dyn, c.status);
+    EpiStore<DAG> epi{in, out, c.cis_f, c.V, c.Nt, 0.f};
+    const WideGeom g = wide_geom(W);
+    const int nsi = (c.V + W - 1) / W;
+    const int i0 = (blockIdx.x % nsi) * W, t0 = (blockIdx.x / nsi) * ns_tile;
+    const int ns = min(ns_tile, c.Nt - t0);
+    SrcSplitW src{&uhi, &ulo, inv, wide_u_rows(ns_tile)};
+    tc_wtile<DAG>(st, g, &mhi, &mlo, c.V, c.Nt, c.Vp, i0, t0, ns, src, 1.f, 1.f, c.e_inv, epi);
+    tc_teardown(st);
+}
+
 // ---------------------------------------------------------------- mixed CG
 struct MixedResult {
     int iterations;
@@ -282,6 +338,7 @@ struct PersistentArgs {
     int cluster;       // > 1: launched in clusters of this size, the inner team is cluster 0
     int res_b;         // streaming layout: resident B per slice tile (apply_team)
     int mode;          // OperandMode: resident needs inner a multiple of the site blocks
+    int wide_W;        // kSlice: sites per slice-major tile
     int vec_resident;  // resident mode with one CTA: FP32 CG vectors in shared memory
     double tol;
     int max_iter;
@@ -290,7 +347,8 @@ struct PersistentArgs {
 
 struct BatchItem {
     ChainView v;
-    const CUtensorMap* maps;   // [0] E_hi, [1] E_lo (global memory, 64-byte aligned)
+    const CUtensorMap* maps;   // [0] E_hi, [1] E_lo, [2] / [3] scaled split for the
+                               // slice-major tile (global memory, 64-byte aligned)
     PersistentArgs pa;
     TrajArgs a;                // n_md, eps, tol, max_iter, chain; seed/traj/phi per call
     long long offset;          // of this chain's field in the packed array
@@ -376,11 +434,16 @@ __device__ __forceinline__ void cg_after_r(CgScalars& s, float rr_new) {
     s.reason = rs;
 }
 
-template <bool SMALL>
+// Kernel kinds of the FP32 iterations: site-major tensor-core tiles, the
+// CUDA-core cluster solver, slice-major tensor-core tiles.
+enum TileKind : int { kKindSite = 0, kKindSmall = 1, kKindSlice = 2 };
+
+template <int KIND>
 __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& sm64,
                          const CUtensorMap* mhi, const CUtensorMap* mlo,
                          const PersistentArgs& pa, ClusterSync* ics, const double2* chi,
                          double2* x64, MixedResult& res) {
+    constexpr bool SMALL = KIND == kKindSmall;
     float2 *rf = c.r_f, *pf = c.p_f, *pn = c.p2_f, *qf = c.q_f, *xf = c.x_f;
     const int inner_size = min(max(pa.inner, 1), tm.size);
     const bool in_inner = tm.rank < inner_size;
@@ -525,9 +588,14 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
                 // p_new = r + beta p; q = M^dag p_new
                 SrcDirection dir{rf, c.r, pf, s_cg.beta, refresh, c.V};
                 EpiDirection ed{dir, pn, rf, qf, cisf, c.Nt, 0.f};
-                if (!apply_team<true>(c, ti, st, mhi, mlo, pa.ns_tile, dir, s_cg.sc, s_cg.inv,
-                                      ed, pa.res_b != 0))
-                    return false;
+                bool aok;
+                if constexpr (KIND == kKindSlice)
+                    aok = apply_team_w<true>(c, ti, st, pa.wide_W, mhi, mlo, pa.ns_tile, dir,
+                                             s_cg.sc, s_cg.inv, ed);
+                else
+                    aok = apply_team<true>(c, ti, st, mhi, mlo, pa.ns_tile, dir, s_cg.sc,
+                                           s_cg.inv, ed, pa.res_b != 0);
+                if (!aok) return false;
                 float qq;
                 if (!team_sum_f(ti, ed.acc, qq)) return false;
                 float2* t = pf;
@@ -540,9 +608,13 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
                 // Ap = M q; x += alpha p; r -= alpha Ap
                 SrcPhase srcq{qf, cisf, c.V};
                 EpiCgUpdate eu{qf, pf, xf, rf, s_cg.alpha, c.V, 0.f};
-                if (!apply_team<false>(c, ti, st, mhi, mlo, pa.ns_tile, srcq, s_cg.sc, s_cg.inv,
-                                       eu, pa.res_b != 0))
-                    return false;
+                if constexpr (KIND == kKindSlice)
+                    aok = apply_team_w<false>(c, ti, st, pa.wide_W, mhi, mlo, pa.ns_tile, srcq,
+                                              s_cg.sc, s_cg.inv, eu);
+                else
+                    aok = apply_team<false>(c, ti, st, mhi, mlo, pa.ns_tile, srcq, s_cg.sc,
+                                            s_cg.inv, eu, pa.res_b != 0);
+                if (!aok) return false;
                 float rr_new;
                 if (!team_sum_f(ti, eu.acc, rr_new)) return false;
                 if (threadIdx.x == 0) cg_after_r(s_cg, rr_new);
@@ -644,35 +716,35 @@ __device__ inline void persistent_teardown(TcState& st) {
 }
 
 // scalars: [0] iterations [1] true residual [2] status [3] reliable updates
-// SMALL: the FP32 iterations run in the CUDA-core cluster mode.
-template <bool SMALL>
+// KIND: TileKind of the FP32 iterations.
+template <int KIND>
 __global__ void __launch_bounds__(NTHR, 1)
     k_cg(const __grid_constant__ CUtensorMap mhi, const __grid_constant__ CUtensorMap mlo,
          ChainView c, PersistentArgs pa, const double* phi, const double2* chi, double2* x) {
     extern __shared__ __align__(1024) uint8_t dyn[];
     __shared__ f64::Smem sm64;
     TcState st;
-    persistent_setup<SMALL>(st, dyn, c.status);
+    persistent_setup<KIND == kKindSmall>(st, dyn, c.status);
     __shared__ ClusterSync s_cs;
     Team tm = make_team(c);
     cluster_begin(pa, &s_cs, c.status);
     set_phases(c, tm, phi);
     MixedResult res{};
     bool ok = team_barrier(tm);
-    if (ok) ok = cg_mixed<SMALL>(c, tm, st, sm64, &mhi, &mlo, pa, &s_cs, chi, x, res);
+    if (ok) ok = cg_mixed<KIND>(c, tm, st, sm64, &mhi, &mlo, pa, &s_cs, chi, x, res);
     if (ok && tm.rank == 0 && threadIdx.x == 0) {
         c.scalars[0] = res.iterations;
         c.scalars[1] = res.true_res;
         c.scalars[2] = res.status;
         c.scalars[3] = res.reliable_updates;
     }
-    persistent_teardown<SMALL>(st);
+    persistent_teardown<KIND == kKindSmall>(st);
     if (pa.cluster > 1) cluster_barrier_all();   // no member leaves while others may push
 }
 
 // One HMC trajectory with the mixed solver (same steps as the FP64 one),
 // run by team `tm`; results in c.scalars.  Returns false if the team failed.
-template <bool SMALL>
+template <int KIND>
 __device__ bool run_trajectory(const ChainView& c, Team& tm, TcState& st, f64::Smem& sm64,
                                const CUtensorMap* mhi, const CUtensorMap* mlo,
                                const PersistentArgs& pa, ClusterSync* ics, const TrajArgs& a) {
@@ -724,7 +796,7 @@ __device__ bool run_trajectory(const ChainView& c, Team& tm, TcState& st, f64::S
             if (!(ok = team_barrier(tm))) break;
         }
         MixedResult res{};
-        if (!(ok = cg_mixed<SMALL>(c, tm, st, sm64, mhi, mlo, pa, ics, c.chi, c.x, res))) break;
+        if (!(ok = cg_mixed<KIND>(c, tm, st, sm64, mhi, mlo, pa, ics, c.chi, c.x, res))) break;
         iters += res.iterations;
         rus += res.reliable_updates;
         ++solves;
@@ -770,7 +842,7 @@ __device__ bool run_trajectory(const ChainView& c, Team& tm, TcState& st, f64::S
     return ok;
 }
 
-template <bool SMALL>
+template <int KIND>
 __global__ void __launch_bounds__(NTHR, 1)
     k_trajectory(const __grid_constant__ CUtensorMap mhi,
                  const __grid_constant__ CUtensorMap mlo, ChainView c, PersistentArgs pa,
@@ -778,12 +850,12 @@ __global__ void __launch_bounds__(NTHR, 1)
     extern __shared__ __align__(1024) uint8_t dyn[];
     __shared__ f64::Smem sm64;
     TcState st;
-    persistent_setup<SMALL>(st, dyn, c.status);
+    persistent_setup<KIND == kKindSmall>(st, dyn, c.status);
     __shared__ ClusterSync s_cs;
     Team tm = make_team(c);
     cluster_begin(pa, &s_cs, c.status);
-    run_trajectory<SMALL>(c, tm, st, sm64, &mhi, &mlo, pa, &s_cs, a);
-    persistent_teardown<SMALL>(st);
+    run_trajectory<KIND>(c, tm, st, sm64, &mhi, &mlo, pa, &s_cs, a);
+    persistent_teardown<KIND == kKindSmall>(st);
     if (pa.cluster > 1) cluster_barrier_all();   // no member leaves while others may push
 }
 
@@ -813,11 +885,10 @@ __global__ void __launch_bounds__(NTHR, 1)
             for (int k = 0; k < kNumScalars; ++k) it.v.scalars[k] = 0.0;
             // the maps live in global memory: make them visible to the TMA
             // (async) proxy of the thread that issues the tile loads
-            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(it.maps)
-                         : "memory");
-            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
-                             it.maps + 1)
-                         : "memory");
+            for (int m = 0; m < 4; ++m)
+                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                                 it.maps + m)
+                             : "memory");
         }
         __syncthreads();
         Team tm;
@@ -832,11 +903,16 @@ __global__ void __launch_bounds__(NTHR, 1)
         a.seed = call->seed;
         a.traj = call->traj;
         a.phi = call->phi + it.offset;
-        const bool ok =
-            it.pa.mode == kSmall
-                ? run_trajectory<true>(it.v, tm, st, sm64, it.maps, it.maps + 1, it.pa, nullptr, a)
-                : run_trajectory<false>(it.v, tm, st, sm64, it.maps, it.maps + 1, it.pa, nullptr,
-                                        a);
+        bool ok;
+        if (it.pa.mode == kSmall)
+            ok = run_trajectory<kKindSmall>(it.v, tm, st, sm64, it.maps, it.maps + 1, it.pa,
+                                            nullptr, a);
+        else if (it.pa.mode == kSlice)
+            ok = run_trajectory<kKindSlice>(it.v, tm, st, sm64, it.maps + 2, it.maps + 3, it.pa,
+                                            nullptr, a);
+        else
+            ok = run_trajectory<kKindSite>(it.v, tm, st, sm64, it.maps, it.maps + 1, it.pa,
+                                           nullptr, a);
         __syncthreads();
         if (threadIdx.x == 0) {
             for (int k = 0; k < kNumScalars; ++k) outs[(size_t)ci * kNumScalars + k] = it.v.scalars[k];
@@ -917,10 +993,32 @@ int tc_ctx_init(hmc_ctx* c) {
             hi[(size_t)r * v.Vp + k] = h;
             lo[(size_t)r * v.Vp + k] = __float2half_rn((float)rem);
         }
+    // slice-major tile: 2^eE E = Ew_hi + Ew_lo (plain remainder) with
+    // max |2^eE E| in [2^14, 2^15)
+    double emax = 0.0;
+    for (size_t k = 0; k < E.size(); ++k) emax = std::max(emax, std::fabs(E[k]));
+    int eE = 0;
+    if (emax > 0.0 && std::isfinite(emax)) {
+        int ex = 0;
+        std::frexp(emax, &ex);   // emax in [2^(ex-1), 2^ex)
+        eE = std::max(-100, std::min(100, 15 - ex));
+    }
+    const double es = std::ldexp(1.0, eE);
+    std::vector<__half> whi((size_t)v.Vr * v.Vp), wlo((size_t)v.Vr * v.Vp);
+    for (int r = 0; r < v.Vr; ++r)
+        for (int k = 0; k < v.Vp; ++k) {
+            const double e = (r < V && k < V) ? E[(size_t)r * V + k] * es : 0.0;
+            const __half h = __float2half_rn((float)e);
+            whi[(size_t)r * v.Vp + k] = h;
+            wlo[(size_t)r * v.Vp + k] = __float2half_rn((float)(e - (double)__half2float(h)));
+        }
+    v.e_inv = (float)std::ldexp(1.0, -eE);
     bool ok = true;
     const size_t N = (size_t)v.N;
     void* dhi = dev_alloc(c, hi.size() * sizeof(__half), &ok);
     void* dlo = dev_alloc(c, lo.size() * sizeof(__half), &ok);
+    void* dwhi = dev_alloc(c, whi.size() * sizeof(__half), &ok);
+    void* dwlo = dev_alloc(c, wlo.size() * sizeof(__half), &ok);
     v.cis_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
     v.r_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
     v.p_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
@@ -931,44 +1029,84 @@ int tc_ctx_init(hmc_ctx* c) {
     if (cudaMemcpy(dhi, hi.data(), hi.size() * sizeof(__half), cudaMemcpyHostToDevice) !=
             cudaSuccess ||
         cudaMemcpy(dlo, lo.data(), lo.size() * sizeof(__half), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(dwhi, whi.data(), whi.size() * sizeof(__half), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(dwlo, wlo.data(), wlo.size() * sizeof(__half), cudaMemcpyHostToDevice) !=
             cudaSuccess)
         return HMC_ERR_CUDA;
     v.E_hi = dhi;
     v.E_lo = dlo;
+    v.Ew_hi = dwhi;
+    v.Ew_lo = dwlo;
     c->tc = new TcCtx();
     if (!make_map(&c->tc->map_hi, dhi, v.Vr, v.Vp) || !make_map(&c->tc->map_lo, dlo, v.Vr, v.Vp))
         return HMC_ERR_CUDA;
+    {
+        // slice-major tiles: all sites in one tile up to 288; standalone
+        // applications above 256 sites take tiles of 144 (one instruction,
+        // same TMA box) and as many slice tiles as fill one wave
+        TcCtx* t = c->tc;
+        t->w_cg = tc::wide_sites(V);
+        const tc::WideGeom g = tc::wide_geom(t->w_cg);
+        const int box = t->w_cg / g.nmma;
+        t->w_apply = V > tc::kWMaxN ? box : t->w_cg;
+        const int nsi = (V + t->w_apply - 1) / t->w_apply;
+        const int per = std::max(1, c->num_sms / nsi);
+        t->ns_wapply = std::max(1, std::min(tc::kWSlices, (v.Nt + per - 1) / per));
+        if (c->params.operand_mode == 4 && c->params.tile_slices > 0)
+            t->ns_wapply = c->params.tile_slices;
+        if (!make_map(&t->map_whi, dwhi, v.Vr, v.Vp, box) ||
+            !make_map(&t->map_wlo, dwlo, v.Vr, v.Vp, box))
+            return HMC_ERR_CUDA;
+    }
     c->tc->ns_apply = pick_ns(v.Vr / tc::TM, v.Nt, c->num_sms);
-    if (c->params.tile_slices > 0) c->tc->ns_apply = c->params.tile_slices;
+    if (c->params.tile_slices > 0 && c->params.operand_mode != 4)
+        c->tc->ns_apply = c->params.tile_slices;
     {
         // pre-split B of standalone applications (rows padded by 64 zero rows)
         const int nb = ((2 * c->tc->ns_apply + 15) / 16) * 16;   // MMA N = TMA box rows
-        c->tc->b_rows = 2 * v.Nt + 64;
+        c->tc->b_rows = 2 * v.Nt + 128;   // a 128-row box from any 2t stays inside
         const size_t nbh = (size_t)c->tc->b_rows * v.Vp;
         bool okb = true;
         c->tc->bhi = (__half*)dev_alloc(c, nbh * sizeof(__half), &okb);
         c->tc->blo = (__half*)dev_alloc(c, nbh * sizeof(__half), &okb);
         c->tc->inv_col = (float*)dev_alloc(c, (size_t)v.Nt * sizeof(float), &okb);
         if (!okb || !make_map(&c->tc->map_bhi, c->tc->bhi, c->tc->b_rows, v.Vp, nb) ||
-            !make_map(&c->tc->map_blo, c->tc->blo, c->tc->b_rows, v.Vp, nb))
+            !make_map(&c->tc->map_blo, c->tc->blo, c->tc->b_rows, v.Vp, nb) ||
+            !make_map(&c->tc->map_uhi, c->tc->bhi, c->tc->b_rows, v.Vp,
+                      tc::wide_u_rows(c->tc->ns_wapply)) ||
+            !make_map(&c->tc->map_ulo, c->tc->blo, c->tc->b_rows, v.Vp,
+                      tc::wide_u_rows(c->tc->ns_wapply)))
             return HMC_ERR_CUDA;
         const int split_smem = V * (int)sizeof(float2);
-        for (const void* k : {(const void*)tc::k_split<false>, (const void*)tc::k_split<true>})
+        for (const void* k : {(const void*)tc::k_split<false, false>,
+                              (const void*)tc::k_split<true, false>,
+                              (const void*)tc::k_split<false, true>,
+                              (const void*)tc::k_split<true, true>})
             if (split_smem > 48 * 1024 &&
                 cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      split_smem) != cudaSuccess)
                 return HMC_ERR_CUDA;
     }
-    const void* kernels[] = {(const void*)tc::k_apply<false>, (const void*)tc::k_apply<true>,
-                             (const void*)tc::k_cg<false>, (const void*)tc::k_trajectory<false>,
-                                 (const void*)tc::k_cg<true>, (const void*)tc::k_trajectory<true>};
+    const void* kernels[] = {(const void*)tc::k_apply<false>,
+                             (const void*)tc::k_apply<true>,
+                             (const void*)tc::k_apply_w<false>,
+                             (const void*)tc::k_apply_w<true>,
+                             (const void*)tc::k_cg<tc::kKindSite>,
+                             (const void*)tc::k_trajectory<tc::kKindSite>,
+                             (const void*)tc::k_cg<tc::kKindSmall>,
+                             (const void*)tc::k_trajectory<tc::kKindSmall>,
+                             (const void*)tc::k_cg<tc::kKindSlice>,
+                             (const void*)tc::k_trajectory<tc::kKindSlice>};
     for (const void* k : kernels)
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tc::kSmemBytes) != cudaSuccess)
             return HMC_ERR_CUDA;
     // the small-lattice mode may run on clusters of up to 16 CTAs (beyond the
     // portable 8); a device that cannot co-schedule them refuses the launch
-    for (const void* k : {(const void*)tc::k_cg<true>, (const void*)tc::k_trajectory<true>})
+    for (const void* k : {(const void*)tc::k_cg<tc::kKindSmall>,
+                          (const void*)tc::k_trajectory<tc::kKindSmall>})
         if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
             cudaSuccess)
             (void)cudaGetLastError();
@@ -983,18 +1121,35 @@ void tc_ctx_free(hmc_ctx* c) {
 int tc_apply(hmc_ctx* c, const double* phi, const float2* in, float2* out, bool dag,
              cudaStream_t s) {
     const ChainView& v = c->view;
-    const int ns = c->tc->ns_apply;
-    const int tiles = (v.Vr / tc::TM) * ((v.Nt + ns - 1) / ns);
     const size_t split_smem = (size_t)v.V * sizeof(float2);
     TcCtx* t = c->tc;
+    if (c->params.operand_mode == 4) {
+        const int W = t->w_apply, ns = t->ns_wapply;
+        const int tiles = ((v.V + W - 1) / W) * ((v.Nt + ns - 1) / ns);
+        if (dag) {
+            tc::k_split<true, true><<<v.Nt, 256, split_smem, s>>>(
+                phi, in, v.cis_f, t->bhi, t->blo, t->inv_col, v.V, v.Vp, v.Nt);
+            tc::k_apply_w<true><<<tiles, tc::NTHR, tc::kSmemBytes, s>>>(
+                t->map_whi, t->map_wlo, t->map_uhi, t->map_ulo, v, W, ns, in, out, t->inv_col);
+        } else {
+            tc::k_split<false, true><<<v.Nt, 256, split_smem, s>>>(
+                phi, in, v.cis_f, t->bhi, t->blo, t->inv_col, v.V, v.Vp, v.Nt);
+            tc::k_apply_w<false><<<tiles, tc::NTHR, tc::kSmemBytes, s>>>(
+                t->map_whi, t->map_wlo, t->map_uhi, t->map_ulo, v, W, ns, in, out, t->inv_col);
+        }
+        return cudaGetLastError() == cudaSuccess ? HMC_OK : HMC_ERR_CUDA;
+    }
+    const int ns = c->tc->ns_apply;
+    const int tiles = (v.Vr / tc::TM) * ((v.Nt + ns - 1) / ns);
     if (dag) {
-        tc::k_split<true><<<v.Nt, 256, split_smem, s>>>(phi, in, v.cis_f, t->bhi, t->blo,
-                                                        t->inv_col, v.V, v.Vp, v.Nt);
+        tc::k_split<true, false><<<v.Nt, 256, split_smem, s>>>(phi, in, v.cis_f, t->bhi, t->blo,
+                                                               t->inv_col, v.V, v.Vp, v.Nt);
         tc::k_apply<true><<<tiles, tc::NTHR, tc::kSmemBytes, s>>>(
             t->map_hi, t->map_lo, t->map_bhi, t->map_blo, v, ns, in, out, t->inv_col);
     } else {
-        tc::k_split<false><<<v.Nt, 256, split_smem, s>>>(phi, in, v.cis_f, t->bhi, t->blo,
-                                                         t->inv_col, v.V, v.Vp, v.Nt);
+        tc::k_split<false, false><<<v.Nt, 256, split_smem, s>>>(phi, in, v.cis_f, t->bhi,
+                                                                t->blo, t->inv_col, v.V, v.Vp,
+                                                                v.Nt);
         tc::k_apply<false><<<tiles, tc::NTHR, tc::kSmemBytes, s>>>(
             t->map_hi, t->map_lo, t->map_bhi, t->map_blo, v, ns, in, out, t->inv_col);
     }
@@ -1046,6 +1201,28 @@ static tc::PersistentArgs persistent_args(hmc_ctx* c, int grid, double tol, int 
         pa.mode = tc::kSmall;
         pa.inner = small_cluster(c);
         pa.ns_tile = 8;
+        pa.vec_resident = 0;
+        pa.tol = tol;
+        pa.max_iter = max_iter;
+        pa.ru_delta = c->params.ru_delta;
+        pa.cluster = 0;
+        pa.res_b = 0;
+        pa.wide_W = 0;
+        return pa;
+    }
+    pa.wide_W = 0;
+    if (c->params.operand_mode == 4) {
+        // slice-major tiles: one CTA per tile at 64 slices by default
+        pa.mode = tc::kSlice;
+        pa.wide_W = c->tc->w_cg;
+        const int nsi = (v.V + pa.wide_W - 1) / pa.wide_W;
+        const int ntt64 = (v.Nt + tc::kWSlices - 1) / tc::kWSlices;
+        pa.inner = std::min(grid, nsi * ntt64);
+        if (c->params.inner_ctas > 0) pa.inner = std::min(c->params.inner_ctas, grid);
+        // slices per tile: balanced over enough slice tiles for the team
+        const int want_tt = std::max(ntt64, (pa.inner + nsi - 1) / nsi);
+        pa.ns_tile = std::min(tc::kWSlices, (v.Nt + want_tt - 1) / want_tt);
+        if (c->params.tile_slices > 0) pa.ns_tile = c->params.tile_slices;
         pa.vec_resident = 0;
         pa.tol = tol;
         pa.max_iter = max_iter;
@@ -1149,28 +1326,35 @@ static int round_grid(const tc::PersistentArgs& pa, int grid) {
 
 int tc_cg(hmc_ctx* c, const double* phi, const double2* chi, double2* x, double tol,
           int max_iter, cudaStream_t s) {
-    int grid = team_size(c, (const void*)tc::k_cg<false>);
+    int grid = team_size(c, (const void*)tc::k_cg<tc::kKindSite>);
     if (grid < 1) return HMC_ERR_CUDA;
     tc::PersistentArgs pa = persistent_args(c, grid, tol, max_iter);
     if (pa.mode == tc::kSmall && pa.inner < 1) return HMC_ERR_UNSUPPORTED;
     grid = round_grid(pa, grid);
-    const void* fn = pa.mode == tc::kSmall ? (const void*)tc::k_cg<true> : (const void*)tc::k_cg<false>;
+    const void* fn = pa.mode == tc::kSmall   ? (const void*)tc::k_cg<tc::kKindSmall>
+                     : pa.mode == tc::kSlice ? (const void*)tc::k_cg<tc::kKindSlice>
+                                             : (const void*)tc::k_cg<tc::kKindSite>;
     ChainView v = c->view;
-    void* args[] = {&c->tc->map_hi, &c->tc->map_lo, &v, &pa, &phi, &chi, &x};
+    const bool sl = pa.mode == tc::kSlice;
+    void* args[] = {sl ? &c->tc->map_whi : &c->tc->map_hi, sl ? &c->tc->map_wlo : &c->tc->map_lo,
+                    &v, &pa, &phi, &chi, &x};
     return launch_persistent(c, fn, grid, args, pa, s);
 }
 
 int tc_trajectory(hmc_ctx* c, const TrajArgs& a, cudaStream_t s) {
-    int grid = team_size(c, (const void*)tc::k_trajectory<false>);
+    int grid = team_size(c, (const void*)tc::k_trajectory<tc::kKindSite>);
     if (grid < 1) return HMC_ERR_CUDA;
     tc::PersistentArgs pa = persistent_args(c, grid, a.tol, a.max_iter);
     if (pa.mode == tc::kSmall && pa.inner < 1) return HMC_ERR_UNSUPPORTED;
     grid = round_grid(pa, grid);
-    const void* fn = pa.mode == tc::kSmall ? (const void*)tc::k_trajectory<true>
-                                           : (const void*)tc::k_trajectory<false>;
+    const void* fn = pa.mode == tc::kSmall   ? (const void*)tc::k_trajectory<tc::kKindSmall>
+                     : pa.mode == tc::kSlice ? (const void*)tc::k_trajectory<tc::kKindSlice>
+                                             : (const void*)tc::k_trajectory<tc::kKindSite>;
     ChainView v = c->view;
     TrajArgs av = a;
-    void* args[] = {&c->tc->map_hi, &c->tc->map_lo, &v, &pa, &av};
+    const bool sl = pa.mode == tc::kSlice;
+    void* args[] = {sl ? &c->tc->map_whi : &c->tc->map_hi, sl ? &c->tc->map_wlo : &c->tc->map_lo,
+                    &v, &pa, &av};
     return launch_persistent(c, fn, grid, args, pa, s);
 }
 
@@ -1243,11 +1427,13 @@ int tc_batch_create(const hmc_params* p, int n, TcBatch** out) {
         tc_batch_destroy(b);
         return st;
     }
-    std::vector<CUtensorMap> maps(2 * n_maps);
+    std::vector<CUtensorMap> maps(4 * n_maps);
     for (int i = 0; i < n; ++i)
         if (leader[i] == i) {
-            maps[2 * map_slot[i]] = b->ctxs[i]->tc->map_hi;
-            maps[2 * map_slot[i] + 1] = b->ctxs[i]->tc->map_lo;
+            maps[4 * map_slot[i]] = b->ctxs[i]->tc->map_hi;
+            maps[4 * map_slot[i] + 1] = b->ctxs[i]->tc->map_lo;
+            maps[4 * map_slot[i] + 2] = b->ctxs[i]->tc->map_whi;
+            maps[4 * map_slot[i] + 3] = b->ctxs[i]->tc->map_wlo;
         }
     std::vector<tc::BatchItem> items(n);
     b->offsets.assign(n + 1, 0);
@@ -1260,6 +1446,9 @@ int tc_batch_create(const hmc_params* p, int n, TcBatch** out) {
         it.v.E = lv.E;
         it.v.E_hi = lv.E_hi;
         it.v.E_lo = lv.E_lo;
+        it.v.Ew_hi = lv.Ew_hi;
+        it.v.Ew_lo = lv.Ew_lo;
+        it.v.e_inv = lv.e_inv;
         it.pa.inner = 1;
         it.pa.cluster = 0;
         {
@@ -1283,6 +1472,17 @@ int tc_batch_create(const hmc_params* p, int n, TcBatch** out) {
                 it.pa.vec_resident = 0;
             }
             it.pa.res_b = res_b_ok(it.v, it.pa.mode, it.pa.ns_tile, 1) ? 1 : 0;
+            it.pa.wide_W = 0;
+            // operand_mode 4: slice-major tiles, balanced slices of at most 64
+            if (c->params.operand_mode == 4) {
+                it.pa.mode = tc::kSlice;
+                it.pa.wide_W = c->tc->w_cg;
+                const int ntt = (it.v.Nt + tc::kWSlices - 1) / tc::kWSlices;
+                it.pa.ns_tile = (it.v.Nt + ntt - 1) / ntt;
+                if (c->params.tile_slices > 0) it.pa.ns_tile = c->params.tile_slices;
+                it.pa.res_b = 0;
+                it.pa.vec_resident = 0;
+            }
         }
         it.pa.tol = c->params.cg_tol;
         it.pa.max_iter = c->params.cg_max_iter;
@@ -1320,7 +1520,7 @@ int tc_batch_create(const hmc_params* p, int n, TcBatch** out) {
                    cudaSuccess))
         ok = false;
     if (ok) {
-        for (int i = 0; i < n; ++i) items[i].maps = b->d_maps + 2 * map_slot[i];
+        for (int i = 0; i < n; ++i) items[i].maps = b->d_maps + 4 * map_slot[i];
         ok = cudaMemcpy(b->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(),
                         cudaMemcpyHostToDevice) == cudaSuccess &&
              cudaMemcpy(b->d_items, items.data(), sizeof(tc::BatchItem) * n,

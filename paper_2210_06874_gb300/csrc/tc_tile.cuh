@@ -30,7 +30,8 @@ constexpr int KCH = 64;         // K per chunk: one 128-byte swizzle row of fp16
 constexpr int NMAX = 64;        // max MMA N (= 2 * slices per tile)
 constexpr int NTHR = 256;       // threads per CTA (8 warps)
 constexpr int kMaxStages = 4;   // deepest operand ring
-constexpr uint32_t kTmemCols = 128;    // main accumulator at 0, correction at 64
+constexpr uint32_t kTmemCols = 512;    // site-major tile: main at 0, correction at 64;
+                                       // slice-major tile (tc_wide.cuh): W columns
 constexpr uint32_t kCorrCol = 64;
 constexpr float kLoScale = 2048.f;     // 2^11
 constexpr float kLoInv = 1.f / 2048.f;
@@ -39,7 +40,7 @@ constexpr uint32_t kAChunkBytes = 2 * kATileBytes;  // E_hi + E_lo
 constexpr uint32_t kBTileBytes = NMAX * 128;        // one chunk of B_hi (or B_lo)
 constexpr uint32_t kBStageBytes = 2 * kBTileBytes;  // streaming B stage (N <= 64)
 constexpr uint32_t kBStageSmall = kBStageBytes / 2; // resident B stage (N <= 32)
-constexpr uint32_t kOperandBytes = 204 * 1024;      // operand area of dynamic smem
+constexpr uint32_t kOperandBytes = 208 * 1024;      // operand area of dynamic smem
 constexpr int kMaxResidentChunks = 4;               // resident E: K <= 256
 // warp roles
 constexpr int kWarpTma = 0;            // lane 0 issues the TMA loads of E
@@ -59,6 +60,9 @@ struct TileBars {
     uint64_t empty[kMaxStages];   // MMA commit: the stage may be refilled
     uint64_t acc_full;            // MMA commit after a tile's last chunk
     uint64_t res_full;            // resident E landed
+    uint64_t wfull[4];            // slice-major ring (tc_wide.cuh): TMA bytes + producers
+    uint64_t wempty[4];           // slice-major ring: MMA commit
+    uint64_t wacc;                // slice-major tile: accumulator complete
     uint32_t tmem_base;
 };
 constexpr size_t kSmemBytes = kOperandBytes + sizeof(TileBars) + 1024;  // + alignment slack
@@ -73,7 +77,9 @@ constexpr size_t kSmemBytes = kOperandBytes + sizeof(TileBars) + 1024;  // + ali
 //              vectors of a chain that one CTA solves alone
 //   small:     no tensor-core tiles; the CUDA-core cluster solver of
 //              small_cg.cuh lays out E^T and its vectors in the area
-enum OperandMode : int { kStreaming = 0, kResident = 1, kSmall = 2 };
+//   slice:     slice-major tiles (tc_wide.cuh): a ring of U + E' stages
+//              from the start of the area, with its own barriers
+enum OperandMode : int { kStreaming = 0, kResident = 1, kSmall = 2, kSlice = 3 };
 
 __device__ __forceinline__ uint8_t* smem_base(uint8_t* dyn) {
     const uint32_t a = smem_u32(dyn);
@@ -118,6 +124,10 @@ struct SrcPlain {                       // u = in
         }
     }
     __device__ __forceinline__ float2 load1(int ts, int k) const { return in[(size_t)ts * V + k]; }
+    // sites k, k+1 (k even, k + 1 < V): one 16-byte load
+    __device__ __forceinline__ float4 load2(int ts, int k) const {
+        return *reinterpret_cast<const float4*>(in + (size_t)ts * V + k);
+    }
 };
 
 struct SrcPhase {                       // u = exp(i phi) * in
@@ -138,6 +148,14 @@ struct SrcPhase {                       // u = exp(i phi) * in
     __device__ __forceinline__ float2 load1(int ts, int k) const {
         const size_t o = (size_t)ts * V + k;
         return cmulf(cis[o], in[o]);
+    }
+    __device__ __forceinline__ float4 load2(int ts, int k) const {
+        const size_t o = (size_t)ts * V + k;
+        const float4 a = *reinterpret_cast<const float4*>(in + o);
+        const float4 c = *reinterpret_cast<const float4*>(cis + o);
+        const float2 u0 = cmulf(make_float2(c.x, c.y), make_float2(a.x, a.y));
+        const float2 u1 = cmulf(make_float2(c.z, c.w), make_float2(a.z, a.w));
+        return make_float4(u0.x, u0.y, u1.x, u1.y);
     }
 };
 
@@ -180,6 +198,17 @@ struct SrcDirection {
     }
     __device__ __forceinline__ float2 load1(int ts, int k) const {
         return one((size_t)ts * V + k);
+    }
+    __device__ __forceinline__ float4 load2(int ts, int k) const {
+        const size_t o = (size_t)ts * V + k;
+        if (refresh) {
+            const float2 a = one(o), b = one(o + 1);
+            return make_float4(a.x, a.y, b.x, b.y);
+        }
+        const float4 a = *reinterpret_cast<const float4*>(r + o);
+        const float4 b = *reinterpret_cast<const float4*>(p_old + o);
+        return make_float4(fmaf(beta, b.x, a.x), fmaf(beta, b.y, a.y), fmaf(beta, b.z, a.z),
+                           fmaf(beta, b.w, a.w));
     }
 };
 
@@ -267,6 +296,8 @@ struct TcState {
     uint32_t gchunk;   // chunks processed so far by this CTA (ring phases)
     uint32_t ntile;    // tiles processed so far (accumulator phases)
     uint32_t nres;     // resident loads so far (phases of res_full)
+    uint32_t wchunk;   // slice-major ring: chunks so far
+    uint32_t wtile;    // slice-major tiles so far
     int* status;
     __device__ __forceinline__ uint8_t* a_hi(int kc, int s) const {
         return base + (mode == kResident ? kc : s) * kAChunkBytes;
@@ -291,6 +322,8 @@ __device__ inline void tc_setup(TcState& st, uint8_t* dyn, int* status) {
     st.gchunk = 0;
     st.ntile = 0;
     st.nres = 0;
+    st.wchunk = 0;
+    st.wtile = 0;
     st.status = status;
     TileBars& b = *st.bars;
     if (threadIdx.x == 0) {
@@ -300,6 +333,11 @@ __device__ inline void tc_setup(TcState& st, uint8_t* dyn, int* status) {
         }
         mbar_init(smem_u32(&b.acc_full), 1);
         mbar_init(smem_u32(&b.res_full), 1);
+        for (int s = 0; s < 4; ++s) {
+            mbar_init(smem_u32(&b.wfull[s]), 1 + kNumBWarps);
+            mbar_init(smem_u32(&b.wempty[s]), 1);
+        }
+        mbar_init(smem_u32(&b.wacc), 1);
         fence_mbar_init();
     }
     if ((threadIdx.x >> 5) == 0) {
@@ -353,6 +391,8 @@ __device__ inline void tc_teardown(TcState& st) {
     TileBars& b = *st.bars;
     if (st.ntile > 0 && *((volatile int*)st.status) != 0)
         mbar_wait(smem_u32(&b.acc_full), (st.ntile - 1) & 1, st.status);
+    if (st.wtile > 0 && *((volatile int*)st.status) != 0)
+        mbar_wait(smem_u32(&b.wacc), (st.wtile - 1) & 1, st.status);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();

@@ -7,12 +7,14 @@ def test_candidates_cover_one_cta_and_tile_teams():
     c = autotune.candidates(p, num_sms=148)
     assert (1, 1, 32, 1) in c and (12, 1, 8, 1) in c and (12, 4, 8, 1) in c
     assert (12, 1, 16, 2) in c                   # resident E, one site block
-    assert all(ns in (8, 16, 32) for _, _, ns, _ in c)
+    assert all(ns in (8, 16, 32) for _, _, ns, m in c if m != 4)
+    assert (12, 1, 0, 4) in c and (12, 8, 0, 4) in c   # slice-major, slices chosen by the library
     assert all(inner <= team <= 148 for team, inner, _, _ in c)
     single = autotune.candidates(p, num_sms=148, single_cta=True)
-    assert single == [(1, 1, 8, 1), (1, 1, 8, 2), (1, 1, 16, 1), (1, 1, 16, 2), (1, 1, 32, 1)]
+    assert single == [(1, 1, 0, 4), (1, 1, 8, 1), (1, 1, 8, 2), (1, 1, 16, 1), (1, 1, 16, 2),
+                      (1, 1, 32, 1)]
     big = autotune.candidates(hmc.Params(L=24, Nt=96, beta=12.0), num_sms=148)
-    assert all(mode == 1 for *_, mode in big)    # E rows too large to stay resident
+    assert all(mode in (1, 4) for *_, mode in big)    # E rows too large to stay resident
 
 
 def test_pick_fastest_then_fewest_ctas():
@@ -22,7 +24,7 @@ def test_pick_fastest_then_fewest_ctas():
 
 def test_small_cluster_mode_candidates():
     """CUDA-core cluster mode (operand_mode 3): clusters of 1, 2, 4, 8 CTAs with
-    at most 16 slices each and the layout inside the 204 KB operand area."""
+    at most 16 slices each and the layout inside the 208 KB operand area."""
     c = autotune.candidates(hmc.Params(L=6, Nt=32, beta=4.0), num_sms=148)
     small = [s for s in c if s[3] == 3]
     assert (8, 8, 8, 3) in small and (2, 2, 8, 3) in small

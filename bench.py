@@ -63,6 +63,9 @@ def parse():
                     help="untimed thermalisation trajectories before warm-up")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--operand-mode", type=int, default=None, choices=[0, 1, 2, 3, 4],
+                    help="apply mode: operand_mode of the mixed path (default: the "
+                         "workload's; 1 site-major tiles, 4 slice-major tiles)")
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     return ap.parse_args()
 
@@ -465,6 +468,8 @@ def run_apply(args):
     build_lib.build()
     name = args.workload
     w, params, prec = workload_params(name, args.precision)
+    if args.operand_mode is not None:
+        params.operand_mode = args.operand_mode
     ctx = hmc.Context(params)
     V, Nt = params.V, params.Nt
     dev = torch.device("cuda", local_rank)
@@ -538,6 +543,7 @@ def run_apply(args):
             "data": "synthetic",
             "config": {"workload": name, "mode": "apply", "precision": prec, "V": V, "Nt": Nt,
                        "applies_per_step": args.applies,
+                       "operand_mode": params.operand_mode,
                        "timing": "one CUDA-graph replay of the step's C-ABI calls",
                        "l2": "flushed (256 MB write + read sweep) between timed steps"},
             "per_call_from_python_us": eager_ms * 1e3,

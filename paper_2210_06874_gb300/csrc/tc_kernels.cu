@@ -35,7 +35,7 @@ struct TcCtx {
     // applications, slices per standalone tile, and the maps of the
     // pre-split U (plain remainder) over bhi / blo with 128-row boxes
     CUtensorMap map_whi, map_wlo, map_uhi, map_ulo;
-    int w_cg, w_apply, ns_wapply;
+    int w_cg, w_apply, ns_wapply, csplit_apply;
 };
 
 namespace tc {
@@ -226,14 +226,17 @@ __device__ bool apply_team_w(const ChainView& c, const Team& tm, TcState& st, in
 // (PLAIN, for the slice-major tile: lo = fp16(s u - hi)) in rows 2t (re) and
 // 2t+1 (im), zero from V to Vp; inv[t] = 2^-e.  Also writes the FP32 phase
 // table of slice t (the M^dag epilogue reads it).
-// Dynamic shared memory: V float2 (the source slice).
+// Dynamic shared memory: V float2 (the source slice).  1024 threads per
+// block: the work per slice is a few sites per thread, so the block's two
+// passes are each about one round trip to memory.
+constexpr int kSplitThreads = 1024;
 template <bool DAG, bool PLAIN>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kSplitThreads)
     k_split(const double* __restrict__ phi, const float2* __restrict__ in,
             float2* __restrict__ cis_f, __half* __restrict__ bhi, __half* __restrict__ blo,
             float* __restrict__ inv, int V, int Vp, int Nt) {
     extern __shared__ float2 u_s[];
-    __shared__ float s_max[8];
+    __shared__ float s_max[kSplitThreads / 32];
     __shared__ int s_e;
     const int t = blockIdx.x;
     const int ts = DAG ? (t + 1 == Nt ? 0 : t + 1) : (t == 0 ? Nt - 1 : t - 1);
@@ -304,23 +307,36 @@ __global__ void __launch_bounds__(NTHR, 1)
     tc_teardown(st);
 }
 
-// Standalone application on slice-major tiles: W sites x ns_tile slices per
-// CTA; E' and the pre-split U arrive by TMA.
+// Standalone application on slice-major tiles: one output tile (W sites x
+// ns_tile slices) per thread-block cluster of csplit CTAs, which split its K
+// chunks; E' and the pre-split U arrive by TMA.  Each CTA contracts its
+// chunks into its own accumulator and stages it in shared memory; after a
+// cluster barrier each takes a share of the tile's outputs, sums the csplit
+// partials through distributed shared memory in rank order and runs the
+// epilogue; a second cluster barrier keeps every CTA's shared memory alive
+// until the others have read it.  csplit = 1 is a plain launch.
 template <bool DAG>
 __global__ void __launch_bounds__(NTHR, 1)
     k_apply_w(const __grid_constant__ CUtensorMap mhi, const __grid_constant__ CUtensorMap mlo,
               const __grid_constant__ CUtensorMap uhi, const __grid_constant__ CUtensorMap ulo,
-              ChainView c, int W, int ns_tile, const float2* in, float2* out, const float* inv) {
+              ChainView c, int W, int ns_tile, int csplit, const float2* in, float2* out,
+              const float* inv) {
     extern __shared__ __align__(1024) uint8_t dyn[];
     TcState st;
     tc_setup(st, dyn, c.status);
     EpiStore<DAG> epi{in, out, c.cis_f, c.V, c.Nt, 0.f};
     const WideGeom g = wide_geom(W);
-    const int nsi = (c.V + W - 1) / W;
-    const int i0 = (blockIdx.x % nsi) * W, t0 = (blockIdx.x / nsi) * ns_tile;
+    const int nsi = (c.V + W - 1) / W, nk = c.Vp / KCH;
+    const int tile = blockIdx.x / csplit, rank = blockIdx.x % csplit;
+    const int i0 = (tile % nsi) * W, t0 = (tile / nsi) * ns_tile;
     const int ns = min(ns_tile, c.Nt - t0);
+    const int kc0 = nk * rank / csplit, kc1 = nk * (rank + 1) / csplit;
     SrcSplitW src{&uhi, &ulo, inv, wide_u_rows(ns_tile)};
-    tc_wtile<DAG>(st, g, &mhi, &mlo, c.V, c.Nt, c.Vp, i0, t0, ns, src, 1.f, 1.f, c.e_inv, epi);
+    tc_wstage<DAG>(st, g, &mhi, &mlo, c.V, c.Nt, i0, t0, ns, kc0, kc1, src, 1.f);
+    cluster_barrier_all();   // every member's partial staged (release / acquire)
+    if (*((volatile int*)c.status) == 0)
+        tc_wepilogue(st, W, c.V, i0, t0, ns, src, 1.f, c.e_inv, epi, rank, csplit);
+    cluster_barrier_all();   // the partials stay until every member has read them
     tc_teardown(st);
 }
 
@@ -1051,11 +1067,17 @@ int tc_ctx_init(hmc_ctx* c) {
         const tc::WideGeom g = tc::wide_geom(t->w_cg);
         const int box = t->w_cg / g.nmma;
         t->w_apply = V > tc::kWMaxN ? box : t->w_cg;
+        // standalone tiles of up to 64 slices (balanced); each tile's K is
+        // split over a cluster of up to 8 CTAs while the tiles x split fill
+        // the GPU (at least one K chunk per CTA)
         const int nsi = (V + t->w_apply - 1) / t->w_apply;
-        const int per = std::max(1, c->num_sms / nsi);
-        t->ns_wapply = std::max(1, std::min(tc::kWSlices, (v.Nt + per - 1) / per));
+        const int ntt = (v.Nt + tc::kWSlices - 1) / tc::kWSlices;
+        t->ns_wapply = (v.Nt + ntt - 1) / ntt;
         if (c->params.operand_mode == 4 && c->params.tile_slices > 0)
             t->ns_wapply = c->params.tile_slices;
+        const int tiles = nsi * ((v.Nt + t->ns_wapply - 1) / t->ns_wapply);
+        t->csplit_apply = std::max(1, std::min(std::min(tc::kMaxClusterW, v.Vp / tc::KCH),
+                                               c->num_sms / std::max(1, tiles)));
         if (!make_map(&t->map_whi, dwhi, v.Vr, v.Vp, box) ||
             !make_map(&t->map_wlo, dwlo, v.Vr, v.Vp, box))
             return HMC_ERR_CUDA;
@@ -1124,30 +1146,45 @@ int tc_apply(hmc_ctx* c, const double* phi, const float2* in, float2* out, bool 
     const size_t split_smem = (size_t)v.V * sizeof(float2);
     TcCtx* t = c->tc;
     if (c->params.operand_mode == 4) {
-        const int W = t->w_apply, ns = t->ns_wapply;
+        int W = t->w_apply, ns = t->ns_wapply, cs = t->csplit_apply;
         const int tiles = ((v.V + W - 1) / W) * ((v.Nt + ns - 1) / ns);
-        if (dag) {
-            tc::k_split<true, true><<<v.Nt, 256, split_smem, s>>>(
+        if (dag)
+            tc::k_split<true, true><<<v.Nt, tc::kSplitThreads, split_smem, s>>>(
                 phi, in, v.cis_f, t->bhi, t->blo, t->inv_col, v.V, v.Vp, v.Nt);
-            tc::k_apply_w<true><<<tiles, tc::NTHR, tc::kSmemBytes, s>>>(
-                t->map_whi, t->map_wlo, t->map_uhi, t->map_ulo, v, W, ns, in, out, t->inv_col);
-        } else {
-            tc::k_split<false, true><<<v.Nt, 256, split_smem, s>>>(
+        else
+            tc::k_split<false, true><<<v.Nt, tc::kSplitThreads, split_smem, s>>>(
                 phi, in, v.cis_f, t->bhi, t->blo, t->inv_col, v.V, v.Vp, v.Nt);
-            tc::k_apply_w<false><<<tiles, tc::NTHR, tc::kSmemBytes, s>>>(
-                t->map_whi, t->map_wlo, t->map_uhi, t->map_ulo, v, W, ns, in, out, t->inv_col);
-        }
-        return cudaGetLastError() == cudaSuccess ? HMC_OK : HMC_ERR_CUDA;
+        if (cudaGetLastError() != cudaSuccess) return HMC_ERR_CUDA;
+        ChainView vv = v;
+        const float2* inp = in;
+        float2* outp = out;
+        const float* invp = t->inv_col;
+        void* args[] = {&t->map_whi, &t->map_wlo, &t->map_uhi, &t->map_ulo, &vv,
+                        &W, &ns, &cs, &inp, &outp, &invp};
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(tiles * cs);
+        cfg.blockDim = dim3(tc::NTHR);
+        cfg.dynamicSmemBytes = tc::kSmemBytes;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)cs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = cs > 1 ? 1 : 0;
+        const void* fn = dag ? (const void*)tc::k_apply_w<true> : (const void*)tc::k_apply_w<false>;
+        return cudaLaunchKernelExC(&cfg, fn, args) == cudaSuccess ? HMC_OK : HMC_ERR_CUDA;
     }
     const int ns = c->tc->ns_apply;
     const int tiles = (v.Vr / tc::TM) * ((v.Nt + ns - 1) / ns);
     if (dag) {
-        tc::k_split<true, false><<<v.Nt, 256, split_smem, s>>>(phi, in, v.cis_f, t->bhi, t->blo,
+        tc::k_split<true, false><<<v.Nt, tc::kSplitThreads, split_smem, s>>>(phi, in, v.cis_f, t->bhi, t->blo,
                                                                t->inv_col, v.V, v.Vp, v.Nt);
         tc::k_apply<true><<<tiles, tc::NTHR, tc::kSmemBytes, s>>>(
             t->map_hi, t->map_lo, t->map_bhi, t->map_blo, v, ns, in, out, t->inv_col);
     } else {
-        tc::k_split<false, false><<<v.Nt, 256, split_smem, s>>>(phi, in, v.cis_f, t->bhi,
+        tc::k_split<false, false><<<v.Nt, tc::kSplitThreads, split_smem, s>>>(phi, in, v.cis_f, t->bhi,
                                                                 t->blo, t->inv_col, v.V, v.Vp,
                                                                 v.Nt);
         tc::k_apply<false><<<tiles, tc::NTHR, tc::kSmemBytes, s>>>(

@@ -45,6 +45,7 @@ constexpr int kWMaxW = 288;                  // sites per tile (TMEM columns)
 constexpr int kWMaxN = 256;                  // MMA N per instruction
 constexpr uint32_t kUTileBytes = WM * 128;   // one 64-wide K chunk of U_hi (or U_lo)
 constexpr int kWMaxStages = 4;
+constexpr int kMaxClusterW = 8;              // CTAs splitting one tile's K (portable cluster)
 static_assert(kWMaxW <= (int)kTmemCols, "one accumulator of W columns");
 static_assert(2 * (2 * kUTileBytes + 2 * 128 * kWMaxW) <= kOperandBytes, "two wide stages");
 
@@ -142,18 +143,24 @@ struct SrcSplitW {
     int rows;     // TMA box rows of the U maps (2 x slices per tile, <= 128)
 };
 
-// One slice-major tile: target slices t0..t0+ns-1 (ns <= 64), sites
-// i0..i0+W-1.  Epi::load / Epi::store as for tc_tile; store receives
-// w = (E u)_i for the source of target slice t.  e_inv = 2^-eE undoes the
-// scale of E'.  Returns false if a bounded wait failed (status set).  All
-// threads call it; the wide ring uses its own barriers and counters.
-template <bool DAG, class Src, class Epi>
-__device__ bool tc_wtile(TcState& st, const WideGeom& g, const CUtensorMap* mhi,
-                         const CUtensorMap* mlo, int V, int Nt, int Vp, int i0, int t0, int ns,
-                         const Src& src, float scale, float inv_scale, float e_inv, Epi& epi) {
+// Staged accumulator of a slice-major tile: FP32 complex rows [slice][site]
+// at the start of the operand area, row stride W * 8 + 16 bytes (the two
+// half-warps' rows fall on different banks).
+__device__ __forceinline__ int wide_row_floats(int W) { return 2 * W + 4; }
+
+// Contraction part of one slice-major tile: target slices t0..t0+ns-1
+// (ns <= 64), sites i0..i0+W-1, K chunks [kc0, kc1).  Runs the ring (TMA,
+// MMA, U producers), waits for the accumulator and stages it as FP32
+// complex rows [slice][site] in the (then idle) ring.  Returns false if a
+// bounded wait failed (status set).  All threads call it and leave it after
+// a block barrier; the wide ring uses its own barriers and counters.
+template <bool DAG, class Src>
+__device__ bool tc_wstage(TcState& st, const WideGeom& g, const CUtensorMap* mhi,
+                          const CUtensorMap* mlo, int V, int Nt, int i0, int t0, int ns,
+                          int kc0, int kc1, const Src& src, float scale) {
     TileBars& bars = *st.bars;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nk = Vp / KCH;
+    const int nk = kc1 - kc0;
     const int W = g.W, Wm = W / g.nmma, S = g.stages;
     const uint32_t g0 = st.wchunk;
     bool ok = true;
@@ -161,8 +168,9 @@ __device__ bool tc_wtile(TcState& st, const WideGeom& g, const CUtensorMap* mhi,
 
     if (warp == kWarpTma) {
         if (lane == 0) {
-            for (int kc = 0; kc < nk && ok; ++kc) {
-                const uint32_t gc = g0 + kc, s = gc % S, n = gc / S;
+            for (int j = 0; j < nk && ok; ++j) {
+                const int kc = kc0 + j;
+                const uint32_t gc = g0 + j, s = gc % S, n = gc / S;
                 if (n > 0) ok = mbar_wait(smem_u32(&bars.wempty[s]), (n - 1) & 1, st.status);
                 if (!ok) break;
                 const uint32_t bar = smem_u32(&bars.wfull[s]);
@@ -186,8 +194,9 @@ __device__ bool tc_wtile(TcState& st, const WideGeom& g, const CUtensorMap* mhi,
         if (lane == 0) {
             const uint32_t idesc = idesc_f16(WM, Wm);
             const uint32_t tmem = bars.tmem_base;
-            for (int kc = 0; kc < nk && ok; ++kc) {
-                const uint32_t gc = g0 + kc, s = gc % S, n = gc / S;
+            for (int j = 0; j < nk && ok; ++j) {
+                const int kc = kc0 + j;
+                const uint32_t gc = g0 + j, s = gc % S, n = gc / S;
                 ok = mbar_wait(smem_u32(&bars.wfull[s]), n & 1, st.status);
                 if (!ok) break;
                 fence_after_sync();
@@ -196,7 +205,7 @@ __device__ bool tc_wtile(TcState& st, const WideGeom& g, const CUtensorMap* mhi,
 #pragma unroll
                 for (int kk = 0; kk < KCH / 16; ++kk) {
                     const uint32_t off = kk * 32;
-                    const uint32_t acc = (kc | kk) != 0;
+                    const uint32_t acc = (j | kk) != 0;
                     for (int m = 0; m < g.nmma; ++m) {
                         const uint32_t bo = (uint32_t)(m * Wm) * 128u + off;
                         const uint32_t d = tmem + (uint32_t)(m * Wm);
@@ -213,8 +222,9 @@ __device__ bool tc_wtile(TcState& st, const WideGeom& g, const CUtensorMap* mhi,
         // U producers (warps 2..7): each waits for the stage, builds its
         // items (unless the TMA loads U) and arrives once per chunk
         const int pw = warp - kFirstBWarp;
-        for (int kc = 0; kc < nk && ok; ++kc) {
-            const uint32_t gc = g0 + kc, s = gc % S, n = gc / S;
+        for (int j = 0; j < nk && ok; ++j) {
+            const int kc = kc0 + j;
+            const uint32_t gc = g0 + j, s = gc % S, n = gc / S;
             if (n > 0) ok = mbar_wait(smem_u32(&bars.wempty[s]), (n - 1) & 1, st.status);
             if (!ok) break;
             if constexpr (!Src::kTma) {
@@ -231,15 +241,11 @@ __device__ bool tc_wtile(TcState& st, const WideGeom& g, const CUtensorMap* mhi,
         }
     }
     __syncwarp();
-    // epilogue.  Once the accumulator is complete the ring is free: stage D
-    // there as FP32 complex rows [slice][site] (row stride W * 8 + 16 bytes,
-    // so the two half-warps' rows fall on different banks), then let each
-    // warp take whole slices with lanes along the sites, so the epilogue's
-    // global loads and stores are contiguous over the warp.
+    // once the accumulator is complete the ring is free: stage D there
     if (ok) ok = mbar_wait(smem_u32(&bars.wacc), st.wtile & 1, st.status);
     fence_after_sync();
     ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld below is warp-collective
-    const int rs = 2 * W + 4;           // staged row stride in floats
+    const int rs = wide_row_floats(W);
     float* ds = reinterpret_cast<float*>(st.base);
     if (ok) {
         // TMEM lane quarter q = warp % 4 (rows 32q..32q+31 = slices
@@ -270,37 +276,100 @@ __device__ bool tc_wtile(TcState& st, const WideGeom& g, const CUtensorMap* mhi,
                 dst[e] = make_float4(o[4 * e], o[4 * e + 1], o[4 * e + 2], o[4 * e + 3]);
         }
     }
+    st.wchunk = g0 + nk;
+    st.wtile += 1;
+    fence_before_sync();
     __syncthreads();
-    if (*((volatile int*)st.status) == 0) {
-        // segments of 32 sites of one slice, dealt to the warps; UN of them
-        // in flight per warp
-        using In = typename Epi::In;
-        constexpr int UN = 3;
-        const int nseg = (W + 31) / 32, total = ns * nseg;
-        for (int base = warp; base < total; base += UN * (NTHR / 32)) {
-            In in[UN];
+    fence_after_sync();
+    return ok;
+}
+
+// Epilogue of a slice-major tile from staged accumulators: segments of 32
+// sites of one slice, dealt to the warps with the lanes along the sites
+// (the epilogue's global traffic is contiguous over each warp), UN of them
+// in flight per warp.  With csize > 1 the tile's K was split over the
+// csize CTAs of a thread-block cluster: this CTA (cluster rank `rank`)
+// takes its share of the segments and sums the csize staged partials
+// through distributed shared memory in rank order (deterministic); the
+// caller brackets it with cluster barriers.
+template <class Src, class Epi>
+__device__ void tc_wepilogue(const TcState& st, int W, int V, int i0, int t0, int ns,
+                             const Src& src, float inv_scale, float e_inv, Epi& epi, int rank,
+                             int csize) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rs = wide_row_floats(W);
+    const float* ds = reinterpret_cast<const float*>(st.base);
+    const uint32_t ds_s = smem_u32(ds);
+    using In = typename Epi::In;
+    constexpr int UN = 3;
+    const int nseg = (W + 31) / 32, total = ns * nseg;
+    const int s0 = (int)((long long)total * rank / csize);
+    const int s1 = (int)((long long)total * (rank + 1) / csize);
+    for (int base = s0 + warp; base < s1; base += UN * (NTHR / 32)) {
+        In in[UN];
 #pragma unroll
-            for (int u = 0; u < UN; ++u) {
-                const int sg = base + u * (NTHR / 32);
-                const int tt = sg / nseg, n = (sg - tt * nseg) * 32 + lane;
-                if (sg < total && n < W && i0 + n < V) in[u] = epi.load(i0 + n, t0 + tt);
-            }
+        for (int u = 0; u < UN; ++u) {
+            const int sg = base + u * (NTHR / 32);
+            const int tt = sg / nseg, n = (sg - tt * nseg) * 32 + lane;
+            if (sg < s1 && n < W && i0 + n < V) in[u] = epi.load(i0 + n, t0 + tt);
+        }
 #pragma unroll
-            for (int u = 0; u < UN; ++u) {
-                const int sg = base + u * (NTHR / 32);
-                const int tt = sg / nseg, n = (sg - tt * nseg) * 32 + lane;
-                if (sg < total && n < W && i0 + n < V) {
-                    float is = inv_scale * e_inv;
-                    if constexpr (Src::kTma) is = src.inv[t0 + tt] * e_inv;
-                    const float2 d = reinterpret_cast<const float2*>(ds + tt * rs)[n];
-                    epi.store(i0 + n, t0 + tt, in[u], make_float2(d.x * is, d.y * is));
+        for (int u = 0; u < UN; ++u) {
+            const int sg = base + u * (NTHR / 32);
+            const int tt = sg / nseg, n = (sg - tt * nseg) * 32 + lane;
+            if (sg < s1 && n < W && i0 + n < V) {
+                float is = inv_scale * e_inv;
+                if constexpr (Src::kTma) is = src.inv[t0 + tt] * e_inv;
+                float2 d;
+                if (csize == 1) {
+                    d = reinterpret_cast<const float2*>(ds + tt * rs)[n];
+                } else {
+                    d = make_float2(0.f, 0.f);
+                    const uint32_t off = ds_s + (uint32_t)((tt * rs + 2 * n) * 4);
+                    // non-volatile loads (the sums may trail them, so the
+                    // members' loads can be in flight together); the memory
+                    // clobber keeps them after the caller's cluster barrier
+                    float x[kMaxClusterW], y[kMaxClusterW];
+#pragma unroll
+                    for (int qr = 0; qr < kMaxClusterW; ++qr) {
+                        if (qr < csize) {
+                            uint32_t ra;
+                            asm("mapa.shared::cluster.u32 %0, %1, %2;"
+                                : "=r"(ra)
+                                : "r"(off), "r"(qr));
+                            asm("ld.shared::cluster.v2.f32 {%0, %1}, [%2];"
+                                : "=f"(x[qr]), "=f"(y[qr])
+                                : "r"(ra)
+                                : "memory");
+                        }
+                    }
+#pragma unroll
+                    for (int qr = 0; qr < kMaxClusterW; ++qr) {
+                        if (qr < csize) {
+                            d.x += x[qr];
+                            d.y += y[qr];
+                        }
+                    }
                 }
+                epi.store(i0 + n, t0 + tt, in[u], make_float2(d.x * is, d.y * is));
             }
         }
     }
+}
+
+// One slice-major tile on one CTA: contraction over all K, then the
+// epilogue.  Epi::load / Epi::store as for tc_tile; store receives
+// w = (E u)_i for the source of target slice t.  e_inv = 2^-eE undoes the
+// scale of E'.  Returns false if a bounded wait failed (status set).  All
+// threads call it.
+template <bool DAG, class Src, class Epi>
+__device__ bool tc_wtile(TcState& st, const WideGeom& g, const CUtensorMap* mhi,
+                         const CUtensorMap* mlo, int V, int Nt, int Vp, int i0, int t0, int ns,
+                         const Src& src, float scale, float inv_scale, float e_inv, Epi& epi) {
+    tc_wstage<DAG>(st, g, mhi, mlo, V, Nt, i0, t0, ns, 0, Vp / KCH, src, scale);
+    if (*((volatile int*)st.status) == 0)
+        tc_wepilogue(st, g.W, V, i0, t0, ns, src, inv_scale, e_inv, epi, 0, 1);
     fence_proxy_async();   // the next tile's TMA writes where D was staged
-    st.wchunk = g0 + nk;
-    st.wtile += 1;
     fence_before_sync();
     __syncthreads();
     fence_after_sync();

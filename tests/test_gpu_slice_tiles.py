@@ -172,3 +172,17 @@ def test_batch_slice_major_matches_single_chains_and_oracle():
         assert outs[i].max_true_residual <= 1e-10
         assert abs(outs[i].dH - want["dH"]) < 1e-7
         assert bool(outs[i].accept) == want["accept"]
+
+
+def test_apply_slice_major_split_k_deterministic():
+    """Standalone applications split each tile's K over a cluster and sum
+    the partials in rank order: repeated applications are bitwise equal
+    (L = 24: 18 K chunks over 8 CTAs, ragged)."""
+    L, Nt = 24, 96
+    V = 2 * L * L
+    c = hmc.Context(hmc.Params(L=L, Nt=Nt, beta=12.0, U=4.0, operand_mode=4))
+    phi = dev(synth.gaussian_field(8, Nt, V, 0.5))
+    psi = dev(synth.complex_gaussian(9, Nt, V), torch.complex64)
+    a = c.apply_Mdag(phi, psi, prec=hmc.PREC_MIXED)
+    b = c.apply_Mdag(phi, psi, prec=hmc.PREC_MIXED)
+    assert torch.equal(a, b)

@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--applies", type=int, default=20,
                     help="apply mode: applications of M per step")
     ap.add_argument("--chains", type=int, default=256, help="batch workload: chains")
+    ap.add_argument("--batch-team", type=int, default=4,
+                    help="batch workload: CTAs of the cluster teams that the most expensive "
+                         "chains run on (1: every chain on one CTA)")
     ap.add_argument("--loop-chains", type=int, default=32,
                     help="batch workload: chains timed as a loop of single-chain launches")
     ap.add_argument("--loop-chains-fp64", type=int, default=8,
@@ -318,9 +321,10 @@ def run_ours(args):
     tuned = None
     if prec == "mixed" and not args.no_tune:
         from paper_2210_06874_gb300 import autotune
-        params = autotune.tune(params)
+        params = autotune.tune_ru(autotune.tune(params))
         tuned = {"team_ctas": params.team_ctas, "inner_ctas": params.inner_ctas,
-                 "tile_slices": params.tile_slices, "operand_mode": params.operand_mode}
+                 "tile_slices": params.tile_slices, "operand_mode": params.operand_mode,
+                 "ru_delta": params.ru_delta}
     ctx = hmc.Context(params)
     V, Nt = params.V, params.Nt
     dev = torch.device("cuda", local_rank)
@@ -572,11 +576,15 @@ def run_batch(args):
     shapes = {}
     if not args.no_tune:
         from paper_2210_06874_gb300 import autotune
-        tuned = [autotune.tune(p, single_cta=True) for p in plist]
+        # one-CTA shapes, and cluster teams for the chains that would
+        # otherwise finish last
+        tuned = autotune.batch_shapes(plist, csize=args.batch_team)
         for p in tuned:
             shapes["L%d_Nt%d" % (p.L, p.Nt)] = {"tile_slices": p.tile_slices,
-                                                "operand_mode": p.operand_mode}
-        loop_params = [autotune.tune(p) for p in plist[:args.loop_chains]]
+                                                "operand_mode": p.operand_mode,
+                                                "team_ctas": max(1, p.team_ctas),
+                                                "ru_delta": p.ru_delta}
+        loop_params = [autotune.tune_ru(autotune.tune(p)) for p in plist[:args.loop_chains]]
         plist = tuned
     else:
         loop_params = plist[:args.loop_chains]

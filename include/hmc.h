@@ -79,8 +79,12 @@ typedef struct hmc_params {
     int cg_max_iter;     /* CG iteration cap per solve */
     int precision;       /* hmc_precision used by hmc_trajectory */
     double ru_delta;     /* mixed CG: reliable update when |r| < ru_delta * max|r|
-                            since the last update (0 selects the default) */
-    int team_ctas;       /* CTAs of a persistent launch (0: automatic) */
+                            since the last update (0 selects the default,
+                            0.05) */
+    int team_ctas;       /* CTAs of a persistent launch (0: automatic); in a
+                            batch, 2..8 runs the chain on a thread-block
+                            cluster of that many CTAs (one size per batch;
+                            those chains go first), else one CTA */
     int tile_slices;     /* time slices per tensor-core tile, one of 8, 16, 32
                             (operand_mode 4: 1..64; 0: automatic) */
     int inner_ctas;      /* CTAs running the FP32 iterations of the mixed CG
@@ -233,7 +237,11 @@ int hmc_apply_brs(int L, int Nt, double delta_kappa, const void* cis, const void
  * Chain i uses Philox chain id i. */
 typedef struct hmc_batch hmc_batch;
 
-/* params: host array of n_chains parameter sets. */
+/* params: host array of n_chains parameter sets (mixed precision).  Chains
+ * with team_ctas >= 2 run as thread-block-cluster teams of that many CTAs
+ * (all such chains of a batch must ask for the same size, at most 8;
+ * HMC_ERR_UNSUPPORTED otherwise, or if the chain's launch shape cannot use
+ * all of them as one inner team). */
 int hmc_batch_create(const hmc_params* params, int n_chains, hmc_batch** out);
 int hmc_batch_destroy(hmc_batch* batch);
 

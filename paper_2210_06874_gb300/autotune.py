@@ -36,6 +36,17 @@ def small_feasible(V, Nt, C):
     return total <= 208 * 1024
 
 
+def team_candidates(params, csize):
+    """Shapes for a chain run as a thread-block-cluster team of csize CTAs
+    (a batch's team chains): every CTA in the inner team; slice-major tiles
+    (slices chosen by the library), site-major tiles of 8 or 16 slices, and
+    the CUDA-core cluster mode where the chain fits it."""
+    out = [(csize, csize, 0, 4), (csize, csize, 8, 1), (csize, csize, 16, 1)]
+    if small_feasible(params.V, params.Nt, csize):
+        out.append((csize, csize, 8, 3))
+    return sorted(set(out))
+
+
 def candidates(params, num_sms, single_cta=False):
     """Shapes (team_ctas, inner_ctas, tile_slices, operand_mode) worth timing:
     streamed E with one CTA or teams sized to the tensor-core / FP64 tile
@@ -82,12 +93,13 @@ def pick(timings):
     return min(timings, key=lambda kv: (kv[1],) + tuple(kv[0]))[0]
 
 
-def tune(params, iters=40, reps=2, single_cta=False, seed=1):
-    """Return a copy of params with team_ctas, inner_ctas and tile_slices set
-    to the fastest measured shape."""
-    key = (params.L, params.Nt, round(params.beta / params.Nt, 12), single_cta)
+def tune(params, iters=40, reps=2, single_cta=False, seed=1, team=0):
+    """Return a copy of params with team_ctas, inner_ctas, tile_slices and
+    operand_mode set to the fastest measured shape (team > 1: among the
+    shapes of a cluster team of that many CTAs)."""
+    key = (params.L, params.Nt, round(params.beta / params.Nt, 12), single_cta, team)
     if key in _cache:
-        team, inner, ns, mode = _cache[key]
+        (team_c, inner, ns, mode), _ = _cache[key]
     else:
         dev = torch.device("cuda", torch.cuda.current_device())
         num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -97,8 +109,10 @@ def tune(params, iters=40, reps=2, single_cta=False, seed=1):
         chi = torch.complex(torch.randn(Nt, V, generator=g, dtype=torch.float64),
                             torch.randn(Nt, V, generator=g, dtype=torch.float64)).to(dev)
         timings = []
-        for team, inner, ns, mode in candidates(params, num_sms, single_cta):
-            p = hmc.Params(**{**params.__dict__, "team_ctas": team, "inner_ctas": inner,
+        shapes = team_candidates(params, team) if team > 1 else candidates(params, num_sms,
+                                                                             single_cta)
+        for team_c, inner, ns, mode in shapes:
+            p = hmc.Params(**{**params.__dict__, "team_ctas": team_c, "inner_ctas": inner,
                               "tile_slices": ns, "operand_mode": mode,
                               "precision": hmc.PREC_MIXED})
             ctx = hmc.Context(p)
@@ -117,10 +131,82 @@ def tune(params, iters=40, reps=2, single_cta=False, seed=1):
                              allow_not_converged=True)
             e.record(stream)
             e.synchronize()
-            timings.append(((team, inner, ns, mode),
+            timings.append(((team_c, inner, ns, mode),
                             s.elapsed_time(e) * 1e-3 / (reps * iters)))
             ctx.close()
-        team, inner, ns, mode = pick(timings)
-        _cache[key] = (team, inner, ns, mode)
-    return hmc.Params(**{**params.__dict__, "team_ctas": team, "inner_ctas": inner,
+        best = pick(timings)
+        _cache[key] = (best, dict(timings)[best])
+        team_c, inner, ns, mode = best
+    return hmc.Params(**{**params.__dict__, "team_ctas": team_c, "inner_ctas": inner,
                          "tile_slices": ns, "operand_mode": mode})
+
+
+_ru_cache = {}
+
+
+def tune_ru(params, candidates=(0.01, 0.05, 0.2), seed=2):
+    """Return a copy of params with the reliable-update threshold ru_delta
+    that solves fastest to params.cg_tol, timed with full mixed solves in
+    the params' launch shape (the best value depends on the chain: fewer
+    FP64 updates pay where the FP64 work runs on few CTAs, frequent ones
+    where the FP32 iteration stalls early)."""
+    key = (params.L, params.Nt, round(params.beta / params.Nt, 12), params.team_ctas,
+           params.inner_ctas, params.tile_slices, params.operand_mode, params.cg_tol)
+    if key not in _ru_cache:
+        dev = torch.device("cuda", torch.cuda.current_device())
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        V, Nt = params.V, params.Nt
+        phi = (0.3 * torch.randn(Nt, V, generator=g, dtype=torch.float64)).to(dev)
+        chi = torch.complex(torch.randn(Nt, V, generator=g, dtype=torch.float64),
+                            torch.randn(Nt, V, generator=g, dtype=torch.float64)).to(dev)
+        timings = []
+        for ru in candidates:
+            ctx = hmc.Context(hmc.Params(**{**params.__dict__, "ru_delta": ru,
+                                            "precision": hmc.PREC_MIXED}))
+            try:
+                ctx.cg_solve(phi, chi, tol=params.cg_tol, prec=hmc.PREC_MIXED)
+                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                stream = torch.cuda.current_stream()
+                s.record(stream)
+                ctx.cg_solve(phi, chi, tol=params.cg_tol, prec=hmc.PREC_MIXED)
+                e.record(stream)
+                e.synchronize()
+                timings.append((ru, s.elapsed_time(e)))
+            except hmc.HmcError:
+                pass
+            ctx.close()
+        _ru_cache[key] = min(timings, key=lambda kv: kv[1])[0] if timings else 0.0
+    return hmc.Params(**{**params.__dict__, "ru_delta": _ru_cache[key]})
+
+
+def seconds_per_iteration(params, single_cta=False, team=0):
+    """Measured seconds per CG iteration of the shape tune() chose."""
+    tune(params, single_cta=single_cta, team=team)
+    key = (params.L, params.Nt, round(params.beta / params.Nt, 12), single_cta, team)
+    return _cache[key][1]
+
+
+def plan_teams(estimates, num_ctas, factor=1.0):
+    """Which chains of a batch to run as cluster teams: those whose estimated
+    one-CTA time exceeds factor x the batch's ideal makespan (the sum of the
+    estimates over num_ctas), i.e. the chains that would otherwise finish
+    last.  Returns a list of booleans."""
+    ideal = sum(estimates) / max(1, num_ctas)
+    return [e > factor * ideal for e in estimates]
+
+
+def batch_shapes(plist, csize=4, num_sms=None):
+    """Launch shapes of a batch: each chain's tuned one-CTA shape, or a tuned
+    cluster team of csize CTAs for the chains plan_teams picks, each with its
+    tuned reliable-update threshold.  The one-CTA
+    time of a trajectory is estimated as the tuned seconds per CG iteration
+    times Nt (at fixed delta the iterations per trajectory grow about in
+    proportion to beta = Nt delta)."""
+    if num_sms is None:
+        dev = torch.device("cuda", torch.cuda.current_device())
+        num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    solo = [tune(p, single_cta=True) for p in plist]
+    est = [seconds_per_iteration(p, single_cta=True) * p.Nt for p in plist]
+    teams = plan_teams(est, num_sms) if csize > 1 else [False] * len(plist)
+    shapes = [tune(p, team=csize) if t else s for p, s, t in zip(plist, solo, teams)]
+    return [tune_ru(p) for p in shapes]

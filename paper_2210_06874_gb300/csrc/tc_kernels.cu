@@ -363,6 +363,7 @@ struct PersistentArgs {
 
 struct BatchItem {
     ChainView v;
+    int team;                  // > 1: run by a cluster of this many CTAs (the launch's size)
     const CUtensorMap* maps;   // [0] E_hi, [1] E_lo, [2] / [3] scaled split for the
                                // slice-major tile (global memory, 64-byte aligned)
     PersistentArgs pa;
@@ -876,19 +877,128 @@ __global__ void __launch_bounds__(NTHR, 1)
 }
 
 // ---------------------------------------------------------------- batched
-// Many independent chains of different sizes in one persistent launch: each
-// CTA takes the next chain from an atomic work queue (chains ordered by
-// decreasing estimated cost) and runs its whole trajectory as a one-CTA
-// team; the TMEM allocation and the operand ring persist across chains.
+// Many independent chains of different sizes in one persistent launch,
+// chains ordered by decreasing estimated cost.  With csize == 1 every CTA
+// takes the next chain from an atomic work queue and runs its whole
+// trajectory as a one-CTA team.  With csize > 1 the launch is made of
+// thread-block clusters of csize CTAs and the queue starts with the chains
+// marked as cluster teams (the most expensive ones): while those last, rank
+// 0 of a cluster takes the next chain and hands its index to every member,
+// and the cluster runs it as one team (barriers and sums through
+// distributed shared memory, FP64 steps over all csize CTAs).  At the first
+// one-CTA chain the cluster's members go their own way: rank 0 runs that
+// chain and every member takes further chains alone.  The TMEM allocation
+// and the operand ring persist across chains.
+// One trajectory of a batch chain of kind KIND; not inlined, so each kind
+// is compiled (and given registers) once, whichever phase runs it.
+template <int KIND>
+__device__ __noinline__ bool batch_traj(const BatchItem& it, TcState& st, f64::Smem& sm64,
+                                        Team& tm, ClusterSync* ics, const TrajArgs& a) {
+    const CUtensorMap* m = KIND == kKindSlice ? it.maps + 2 : it.maps;
+    return run_trajectory<KIND>(it.v, tm, st, sm64, m, m + 1, it.pa, ics, a);
+}
+
+__device__ inline void batch_run(const BatchItem& it, int ci, const BatchCallArgs* call,
+                                 double* outs, TcState& st, f64::Smem& sm64, Team& tm,
+                                 ClusterSync* ics, bool write_out, bool& ok) {
+    st.status = it.v.status;
+    TrajArgs a = it.a;
+    a.seed = call->seed;
+    a.traj = call->traj;
+    a.phi = call->phi + it.offset;
+    if (it.pa.mode == kSmall)
+        ok = batch_traj<kKindSmall>(it, st, sm64, tm, ics, a);
+    else if (it.pa.mode == kSlice)
+        ok = batch_traj<kKindSlice>(it, st, sm64, tm, ics, a);
+    else
+        ok = batch_traj<kKindSite>(it, st, sm64, tm, ics, a);
+    __syncthreads();
+    if (write_out && threadIdx.x == 0) {
+        for (int k = 0; k < kNumScalars; ++k)
+            outs[(size_t)ci * kNumScalars + k] = it.v.scalars[k];
+        outs[(size_t)ci * kNumScalars + kTrajStatus] =
+            ok ? it.v.scalars[kTrajStatus] : (double)(*((volatile int*)it.v.status));
+    }
+}
+
+// Reset a chain's status and scalars and make its tensor maps (global
+// memory) visible to the TMA proxy of this CTA.  Thread 0.
+__device__ inline void batch_chain_begin(const BatchItem& it, bool reset) {
+    if (reset) {
+        *it.v.status = 0;
+        for (int k = 0; k < kNumScalars; ++k) it.v.scalars[k] = 0.0;
+    }
+    for (int m = 0; m < 4; ++m)
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(it.maps + m)
+                     : "memory");
+}
+
 __global__ void __launch_bounds__(NTHR, 1)
     k_batch(const BatchItem* __restrict__ items, const int* __restrict__ order, int n,
-            int* queue, const BatchCallArgs* call, double* outs) {
+            int* queue, const BatchCallArgs* call, double* outs, int csize) {
     extern __shared__ __align__(1024) uint8_t dyn[];
     __shared__ f64::Smem sm64;
     __shared__ int s_idx;
+    __shared__ ClusterSync s_cs;
     TcState st;
     tc_setup(st, dyn, items[0].v.status);
-    for (;;) {
+    const int crank = csize > 1 ? (int)cluster_ctarank() : 0;
+    if (csize > 1) cluster_sync_init(&s_cs, csize);
+    bool solo = csize == 1;
+    bool ok = true;
+    // cluster phase: one team chain per cluster at a time
+    while (!solo) {
+        if (crank == 0 && threadIdx.x == 0) {
+            const int v = atomicAdd(queue, 1);
+            if (v < n && items[order[v]].team > 1) batch_chain_begin(items[order[v]], true);
+            const uint32_t la = cta_smem_u32(&s_idx);
+            for (int r = 0; r < csize; ++r) {
+                uint32_t ra;
+                asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(la), "r"(r));
+                asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(ra), "r"(v) : "memory");
+            }
+        }
+        cluster_barrier_all();          // the index (and the chain's reset) published
+        const int idx = s_idx;
+        cluster_barrier_all();          // read by every member before the next write
+        if (idx >= n) break;
+        const int ci = order[idx];
+        const BatchItem& it = items[ci];
+        if (it.team <= 1) {
+            // first one-CTA chain: rank 0 runs it, then all members go alone
+            solo = true;
+            if (crank == 0) {
+                if (threadIdx.x == 0) batch_chain_begin(it, true);
+                __syncthreads();
+                Team tm{};
+                tm.rank = 0;
+                tm.size = 1;
+                tm.bar = it.v.bar;
+                tm.status = it.v.status;
+                tm.partials = it.v.partials;
+                tm.cs = nullptr;
+                batch_run(it, ci, call, outs, st, sm64, tm, nullptr, true, ok);
+            }
+            break;
+        }
+        if (threadIdx.x == 0 && crank != 0) batch_chain_begin(it, false);
+        __syncthreads();
+        Team tm{};
+        tm.rank = crank;
+        tm.size = csize;
+        tm.bar = it.v.bar;
+        tm.status = it.v.status;
+        tm.partials = it.v.partials;
+        tm.cs = &s_cs;
+        batch_run(it, ci, call, outs, st, sm64, tm, &s_cs, crank == 0, ok);
+        // the team's outcome, the same on every member: a failed member has
+        // set the chain's status before it left its waits
+        cluster_barrier_all();
+        ok = *((volatile int*)it.v.status) == 0;
+        if (!ok) break;
+    }
+    // one-CTA phase
+    while (ok) {
         if (threadIdx.x == 0) s_idx = atomicAdd(queue, 1);
         __syncthreads();
         const int idx = s_idx;
@@ -896,50 +1006,21 @@ __global__ void __launch_bounds__(NTHR, 1)
         if (idx >= n) break;
         const int ci = order[idx];
         const BatchItem& it = items[ci];
-        if (threadIdx.x == 0) {
-            *it.v.status = 0;
-            for (int k = 0; k < kNumScalars; ++k) it.v.scalars[k] = 0.0;
-            // the maps live in global memory: make them visible to the TMA
-            // (async) proxy of the thread that issues the tile loads
-            for (int m = 0; m < 4; ++m)
-                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
-                                 it.maps + m)
-                             : "memory");
-        }
+        if (threadIdx.x == 0) batch_chain_begin(it, true);
         __syncthreads();
-        Team tm;
+        Team tm{};
         tm.rank = 0;
         tm.size = 1;
         tm.bar = it.v.bar;
         tm.status = it.v.status;
         tm.partials = it.v.partials;
         tm.cs = nullptr;
-        st.status = it.v.status;
-        TrajArgs a = it.a;
-        a.seed = call->seed;
-        a.traj = call->traj;
-        a.phi = call->phi + it.offset;
-        bool ok;
-        if (it.pa.mode == kSmall)
-            ok = run_trajectory<kKindSmall>(it.v, tm, st, sm64, it.maps, it.maps + 1, it.pa,
-                                            nullptr, a);
-        else if (it.pa.mode == kSlice)
-            ok = run_trajectory<kKindSlice>(it.v, tm, st, sm64, it.maps + 2, it.maps + 3, it.pa,
-                                            nullptr, a);
-        else
-            ok = run_trajectory<kKindSite>(it.v, tm, st, sm64, it.maps, it.maps + 1, it.pa,
-                                           nullptr, a);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int k = 0; k < kNumScalars; ++k) outs[(size_t)ci * kNumScalars + k] = it.v.scalars[k];
-            outs[(size_t)ci * kNumScalars + kTrajStatus] =
-                ok ? it.v.scalars[kTrajStatus] : (double)(*((volatile int*)it.v.status));
-        }
+        batch_run(it, ci, call, outs, st, sm64, tm, nullptr, true, ok);
         // a failed bounded wait leaves the operand ring in an unknown phase:
         // this CTA takes no further chains (they stay unprocessed, status set)
-        if (!ok) break;
     }
     tc_teardown(st);
+    if (csize > 1) cluster_barrier_all();   // no member leaves while others may push to it
 }
 }  // namespace tc
 
@@ -1400,6 +1481,7 @@ int tc_trajectory(hmc_ctx* c, const TrajArgs& a, cudaStream_t s) {
 struct TcBatch {
     int n = 0;
     int grid = 0;
+    int csize = 1;                   // CTAs per cluster (> 1: team chains present)
     std::vector<hmc_ctx*> ctxs;
     std::vector<long long> offsets;   // n + 1
     tc::BatchItem* d_items = nullptr;
@@ -1472,6 +1554,17 @@ int tc_batch_create(const hmc_params* p, int n, TcBatch** out) {
             maps[4 * map_slot[i] + 2] = b->ctxs[i]->tc->map_whi;
             maps[4 * map_slot[i] + 3] = b->ctxs[i]->tc->map_wlo;
         }
+    // chains asking for a team (team_ctas >= 2) run on a thread-block
+    // cluster of that many CTAs; all such chains of a batch use one size
+    for (int i = 0; i < n; ++i) {
+        const int tmc = p[i].team_ctas;
+        if (tmc <= 1) continue;
+        if (tmc > tc::kMaxClusterW || (b->csize > 1 && tmc != b->csize)) {
+            tc_batch_destroy(b);
+            return HMC_ERR_UNSUPPORTED;
+        }
+        b->csize = tmc;
+    }
     std::vector<tc::BatchItem> items(n);
     b->offsets.assign(n + 1, 0);
     std::vector<double> cost(n);
@@ -1486,9 +1579,20 @@ int tc_batch_create(const hmc_params* p, int n, TcBatch** out) {
         it.v.Ew_hi = lv.Ew_hi;
         it.v.Ew_lo = lv.Ew_lo;
         it.v.e_inv = lv.e_inv;
+        it.team = c->params.team_ctas > 1 ? c->params.team_ctas : 1;
         it.pa.inner = 1;
         it.pa.cluster = 0;
-        {
+        if (it.team > 1) {
+            // a cluster team: the launch shape of a single-chain run on
+            // team CTAs with an inner team of all of them, as one cluster
+            if (c->params.inner_ctas == 0) c->params.inner_ctas = it.team;
+            it.pa = persistent_args(c, it.team, c->params.cg_tol, c->params.cg_max_iter);
+            if (it.pa.inner != it.team || (it.pa.mode == tc::kSmall && it.pa.inner < 1)) {
+                tc_batch_destroy(b);
+                return HMC_ERR_UNSUPPORTED;
+            }
+            it.pa.cluster = it.team;
+        } else {
             // one CTA per chain: E resident when the chain has one site block
             const int nti = it.v.Vr / tc::TM, nk = it.v.Vp / tc::KCH;
             const bool res = nti == 1 && nk <= tc::kMaxResidentChunks &&
@@ -1521,6 +1625,7 @@ int tc_batch_create(const hmc_params* p, int n, TcBatch** out) {
                 it.pa.vec_resident = 0;
             }
         }
+        if (it.team > 1) it.pa.res_b = 0;
         it.pa.tol = c->params.cg_tol;
         it.pa.max_iter = c->params.cg_max_iter;
         it.pa.ru_delta = c->params.ru_delta;
@@ -1540,8 +1645,11 @@ int tc_batch_create(const hmc_params* p, int n, TcBatch** out) {
     }
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int c) { return cost[a] > cost[c]; });
+    // team chains first (the cluster phase of the kernel), then by cost
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        if ((items[a].team > 1) != (items[c].team > 1)) return items[a].team > 1;
+        return cost[a] > cost[c];
+    });
     bool ok = true;
     auto alloc = [&](void** ptr, size_t bytes) {
         if (ok && cudaMalloc(ptr, bytes) != cudaSuccess) ok = false;
@@ -1581,6 +1689,29 @@ int tc_batch_create(const hmc_params* p, int n, TcBatch** out) {
         return HMC_ERR_CUDA;
     }
     b->grid = std::min(n, b->ctxs[0]->num_sms * occ);
+    if (b->csize > 1) {
+        // whole clusters, as many as can be resident at once
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(b->ctxs[0]->num_sms / b->csize * b->csize);
+        cfg.blockDim = dim3(tc::NTHR);
+        cfg.dynamicSmemBytes = tc::kSmemBytes;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)b->csize;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclus = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclus, (const void*)tc::k_batch, &cfg) !=
+                cudaSuccess ||
+            nclus < 1) {
+            (void)cudaGetLastError();
+            tc_batch_destroy(b);
+            return HMC_ERR_UNSUPPORTED;
+        }
+        b->grid = nclus * b->csize;
+    }
     *out = b;
     return HMC_OK;
 }
@@ -1607,8 +1738,28 @@ int tc_batch_trajectory(TcBatch* b, double* phi, uint64_t seed, uint64_t traj,
             return HMC_ERR_CUDA;
         cudaMemcpyAsync(b->d_call, b->h_call, sizeof(tc::BatchCallArgs), cudaMemcpyHostToDevice, s);
         cudaMemsetAsync(b->d_queue, 0, sizeof(int), s);
-        tc::k_batch<<<b->grid, tc::NTHR, tc::kSmemBytes, s>>>(b->d_items, b->d_order, b->n,
-                                                            b->d_queue, b->d_call, b->d_outs);
+        {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(b->grid);
+            cfg.blockDim = dim3(tc::NTHR);
+            cfg.dynamicSmemBytes = tc::kSmemBytes;
+            cfg.stream = s;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = (unsigned)b->csize;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = b->csize > 1 ? 1 : 0;
+            const tc::BatchItem* ip = b->d_items;
+            const int* op = b->d_order;
+            int nn = b->n, cs = b->csize;
+            int* qp = b->d_queue;
+            const tc::BatchCallArgs* cp = b->d_call;
+            double* outp = b->d_outs;
+            void* args[] = {&ip, &op, &nn, &qp, &cp, &outp, &cs};
+            cudaLaunchKernelExC(&cfg, (const void*)tc::k_batch, args);
+        }
         cudaMemcpyAsync(b->h_outs, b->d_outs, sizeof(double) * kNumScalars * b->n,
                         cudaMemcpyDeviceToHost, s);
         if (cudaStreamEndCapture(s, &b->graph) != cudaSuccess ||

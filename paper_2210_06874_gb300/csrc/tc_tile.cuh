@@ -296,7 +296,9 @@ struct TcState {
     uint32_t gchunk;   // chunks processed so far by this CTA (ring phases)
     uint32_t ntile;    // tiles processed so far (accumulator phases)
     uint32_t nres;     // resident loads so far (phases of res_full)
-    uint32_t wchunk;   // slice-major ring: chunks so far
+    uint32_t wuse[4];  // slice-major ring: fills of each stage so far (the ring
+                       // depth depends on the tile width, so each stage's
+                       // barrier phases are counted on their own)
     uint32_t wtile;    // slice-major tiles so far
     int* status;
     __device__ __forceinline__ uint8_t* a_hi(int kc, int s) const {
@@ -322,7 +324,7 @@ __device__ inline void tc_setup(TcState& st, uint8_t* dyn, int* status) {
     st.gchunk = 0;
     st.ntile = 0;
     st.nres = 0;
-    st.wchunk = 0;
+    for (int s = 0; s < 4; ++s) st.wuse[s] = 0;
     st.wtile = 0;
     st.status = status;
     TileBars& b = *st.bars;

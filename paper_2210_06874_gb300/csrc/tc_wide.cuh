@@ -46,6 +46,7 @@ constexpr int kWMaxN = 256;                  // MMA N per instruction
 constexpr uint32_t kUTileBytes = WM * 128;   // one 64-wide K chunk of U_hi (or U_lo)
 constexpr int kWMaxStages = 4;
 constexpr int kMaxClusterW = 8;              // CTAs splitting one tile's K (portable cluster)
+static_assert(kWMaxStages <= 4, "TileBars holds four slice-major stages");
 static_assert(kWMaxW <= (int)kTmemCols, "one accumulator of W columns");
 static_assert(2 * (2 * kUTileBytes + 2 * 128 * kWMaxW) <= kOperandBytes, "two wide stages");
 
@@ -162,15 +163,19 @@ __device__ bool tc_wstage(TcState& st, const WideGeom& g, const CUtensorMap* mhi
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = kc1 - kc0;
     const int W = g.W, Wm = W / g.nmma, S = g.stages;
-    const uint32_t g0 = st.wchunk;
     bool ok = true;
+    // chunk j of the tile uses stage j % S (every tile starts at stage 0);
+    // its fill index on that stage is wuse[s] + j / S
+    uint32_t use0[kWMaxStages];
+#pragma unroll
+    for (int s = 0; s < kWMaxStages; ++s) use0[s] = st.wuse[s];
     auto stage = [&](uint32_t s) { return st.base + s * g.stage_bytes; };
 
     if (warp == kWarpTma) {
         if (lane == 0) {
             for (int j = 0; j < nk && ok; ++j) {
                 const int kc = kc0 + j;
-                const uint32_t gc = g0 + j, s = gc % S, n = gc / S;
+                const uint32_t s = (uint32_t)j % S, n = use0[s] + (uint32_t)j / S;
                 if (n > 0) ok = mbar_wait(smem_u32(&bars.wempty[s]), (n - 1) & 1, st.status);
                 if (!ok) break;
                 const uint32_t bar = smem_u32(&bars.wfull[s]);
@@ -196,7 +201,7 @@ __device__ bool tc_wstage(TcState& st, const WideGeom& g, const CUtensorMap* mhi
             const uint32_t tmem = bars.tmem_base;
             for (int j = 0; j < nk && ok; ++j) {
                 const int kc = kc0 + j;
-                const uint32_t gc = g0 + j, s = gc % S, n = gc / S;
+                const uint32_t s = (uint32_t)j % S, n = use0[s] + (uint32_t)j / S;
                 ok = mbar_wait(smem_u32(&bars.wfull[s]), n & 1, st.status);
                 if (!ok) break;
                 fence_after_sync();
@@ -224,7 +229,7 @@ __device__ bool tc_wstage(TcState& st, const WideGeom& g, const CUtensorMap* mhi
         const int pw = warp - kFirstBWarp;
         for (int j = 0; j < nk && ok; ++j) {
             const int kc = kc0 + j;
-            const uint32_t gc = g0 + j, s = gc % S, n = gc / S;
+            const uint32_t s = (uint32_t)j % S, n = use0[s] + (uint32_t)j / S;
             if (n > 0) ok = mbar_wait(smem_u32(&bars.wempty[s]), (n - 1) & 1, st.status);
             if (!ok) break;
             if constexpr (!Src::kTma) {
@@ -276,7 +281,7 @@ __device__ bool tc_wstage(TcState& st, const WideGeom& g, const CUtensorMap* mhi
                 dst[e] = make_float4(o[4 * e], o[4 * e + 1], o[4 * e + 2], o[4 * e + 3]);
         }
     }
-    st.wchunk = g0 + nk;
+    for (int s = 0; s < S; ++s) st.wuse[s] += (uint32_t)((nk + S - 1 - s) / S);
     st.wtile += 1;
     fence_before_sync();
     __syncthreads();

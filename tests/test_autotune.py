@@ -37,3 +37,17 @@ def test_small_cluster_mode_candidates():
     assert not autotune.small_feasible(18, 4, 8)                 # fewer slices than CTAs
     big = autotune.candidates(hmc.Params(L=24, Nt=96, beta=12.0), num_sms=148)
     assert not any(mode == 3 for *_, mode in big)
+
+
+def test_team_candidates_and_plan():
+    """Cluster-team shapes keep every CTA in the inner team; the chains whose
+    one-CTA estimate exceeds the batch's ideal makespan become teams."""
+    p = hmc.Params(L=12, Nt=64, beta=8.0)
+    c = autotune.team_candidates(p, 4)
+    assert (4, 4, 0, 4) in c and (4, 4, 8, 1) in c
+    assert all(team == inner == 4 for team, inner, _, _ in c)
+    assert not any(m == 3 for *_, m in c)                          # V = 288: no CUDA-core mode
+    assert (4, 4, 8, 3) in autotune.team_candidates(hmc.Params(L=6, Nt=32, beta=4.0), 4)
+    est = [10.0, 1.0, 1.0, 1.0, 0.5, 0.5]                        # ideal makespan 14 / 4 = 3.5
+    assert autotune.plan_teams(est, 4) == [True, False, False, False, False, False]
+    assert autotune.plan_teams([1.0] * 8, 4) == [False] * 8       # balanced: no teams

@@ -186,3 +186,32 @@ def test_apply_slice_major_split_k_deterministic():
     a = c.apply_Mdag(phi, psi, prec=hmc.PREC_MIXED)
     b = c.apply_Mdag(phi, psi, prec=hmc.PREC_MIXED)
     assert torch.equal(a, b)
+
+
+def test_batch_reuses_ctas_across_tile_widths():
+    """More chains than CTAs, of four tile widths (W = 16, 32, 80, 176: ring
+    depths 4, 4, 4, 2), so CTAs run several slice-major chains one after the
+    other: every chain converges and matches its single-chain run bitwise."""
+    n = 2 * torch.cuda.get_device_properties(0).multi_processor_count + 8
+    Ls = [2, 3, 6, 9]
+    chains = [(Ls[i % 4], 4 + (i % 3), 2.0 + 0.004 * i) for i in range(n)]
+
+    def p(L, Nt, U, **kw):
+        return hmc.Params(L=L, Nt=Nt, U=U, beta=0.125 * Nt, n_md=2, traj_length=0.2,
+                          cg_tol=1e-10, precision=hmc.PREC_MIXED, operand_mode=4, **kw)
+    b = hmc.Batch([p(*c) for c in chains])
+    phi = torch.zeros(b.total, dtype=torch.float64, device=DEV)
+    fields = [synth.gaussian_field(500 + i, Nt, 2 * L * L, 0.125 * U, scale=0.5)
+              for i, (L, Nt, U) in enumerate(chains)]
+    for i, f in enumerate(fields):
+        b.view(phi, i).copy_(torch.from_numpy(f))
+    outs = b.trajectory(phi, 3, 0)
+    assert all(o.status == 0 for o in outs)
+    assert all(o.max_true_residual <= 1e-10 for o in outs)
+    for i in list(range(0, n, 37)) + [n - 1]:
+        L, Nt, U = chains[i]
+        single = hmc.Context(p(L, Nt, U, team_ctas=1, inner_ctas=1))
+        sphi = torch.from_numpy(fields[i]).to(DEV)
+        o = single.trajectory(sphi, 3, 0, chain=i)
+        assert outs[i].dH == o.dH, (i, outs[i].dH, o.dH)
+        assert torch.equal(b.view(phi, i), sphi)

@@ -186,27 +186,72 @@ def seconds_per_iteration(params, single_cta=False, team=0):
     return _cache[key][1]
 
 
-def plan_teams(estimates, num_ctas, factor=1.0):
-    """Which chains of a batch to run as cluster teams: those whose estimated
-    one-CTA time exceeds factor x the batch's ideal makespan (the sum of the
-    estimates over num_ctas), i.e. the chains that would otherwise finish
-    last.  Returns a list of booleans."""
-    ideal = sum(estimates) / max(1, num_ctas)
-    return [e > factor * ideal for e in estimates]
+def simulate_batch(est_solo, est_team, is_team, num_ctas, csize):
+    """Makespan of one batch step as the kernel schedules it: team chains
+    first, by decreasing estimate, each taken by the next free cluster of
+    csize CTAs; a cluster that finds no team chain left becomes csize
+    independent CTAs; every CTA then takes the one-CTA chains in order of
+    decreasing estimate as it becomes free."""
+    import heapq
+    nclus = num_ctas // csize if csize > 1 else 0
+    teams = sorted((i for i in range(len(est_solo)) if is_team[i]), key=lambda i: -est_team[i])
+    solos = sorted((i for i in range(len(est_solo)) if not is_team[i]), key=lambda i: -est_solo[i])
+    if teams and nclus == 0:
+        return float("inf")
+    clus = [0.0] * nclus
+    heapq.heapify(clus)
+    end = 0.0
+    for i in teams:
+        t = heapq.heappop(clus) + est_team[i]
+        end = max(end, t)
+        heapq.heappush(clus, t)
+    ctas = [t for t in clus for _ in range(csize)] if teams else []
+    ctas += [0.0] * (num_ctas - len(ctas))
+    heapq.heapify(ctas)
+    for i in solos:
+        t = heapq.heappop(ctas) + est_solo[i]
+        end = max(end, t)
+        heapq.heappush(ctas, t)
+    return end
+
+
+def plan_teams(est_solo, est_team, num_ctas, csize):
+    """Which chains of a batch to run as cluster teams: the k most expensive
+    (by one-CTA estimate), k chosen to minimise the simulated makespan.
+    est_team[i] may be None for chains not worth a team.  Returns a list of
+    booleans."""
+    n = len(est_solo)
+    cand = sorted((i for i in range(n) if est_team[i] is not None), key=lambda i: -est_solo[i])
+    best_k, best = 0, simulate_batch(est_solo, est_team, [False] * n, num_ctas, csize)
+    for k in range(1, len(cand) + 1):
+        flags = [False] * n
+        for i in cand[:k]:
+            flags[i] = True
+        m = simulate_batch(est_solo, est_team, flags, num_ctas, csize)
+        if m < best:
+            best_k, best = k, m
+    flags = [False] * n
+    for i in cand[:best_k]:
+        flags[i] = True
+    return flags
 
 
 def batch_shapes(plist, csize=4, num_sms=None):
     """Launch shapes of a batch: each chain's tuned one-CTA shape, or a tuned
     cluster team of csize CTAs for the chains plan_teams picks, each with its
-    tuned reliable-update threshold.  The one-CTA
-    time of a trajectory is estimated as the tuned seconds per CG iteration
-    times Nt (at fixed delta the iterations per trajectory grow about in
-    proportion to beta = Nt delta)."""
+    tuned reliable-update threshold.  The time of a trajectory is estimated
+    as the tuned seconds per CG iteration (one CTA, or the team) times Nt (at
+    fixed delta the iterations per trajectory grow about in proportion to
+    beta = Nt delta); teams are timed only for chains above half the ideal
+    makespan."""
     if num_sms is None:
         dev = torch.device("cuda", torch.cuda.current_device())
         num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
     solo = [tune(p, single_cta=True) for p in plist]
     est = [seconds_per_iteration(p, single_cta=True) * p.Nt for p in plist]
-    teams = plan_teams(est, num_sms) if csize > 1 else [False] * len(plist)
+    ideal = sum(est) / max(1, num_sms)
+    est_team = [seconds_per_iteration(p, team=csize) * p.Nt
+                if csize > 1 and e > 0.5 * ideal else None for p, e in zip(plist, est)]
+    teams = plan_teams(est, est_team, num_sms, csize) if csize > 1 else [False] * len(plist)
     shapes = [tune(p, team=csize) if t else s for p, s, t in zip(plist, solo, teams)]
     return [tune_ru(p) for p in shapes]

@@ -1333,10 +1333,10 @@ static tc::PersistentArgs persistent_args(hmc_ctx* c, int grid, double tol, int 
         // slice-major tiles: one CTA per tile at 64 slices by default
         pa.mode = tc::kSlice;
         pa.wide_W = c->tc->w_cg;
-        const int nsi = (v.V + pa.wide_W - 1) / pa.wide_W;
         const int ntt64 = (v.Nt + tc::kWSlices - 1) / tc::kWSlices;
-        pa.inner = std::min(grid, nsi * ntt64);
+        pa.inner = std::min(grid, ((v.V + pa.wide_W - 1) / pa.wide_W) * ntt64);
         if (c->params.inner_ctas > 0) pa.inner = std::min(c->params.inner_ctas, grid);
+        const int nsi = (v.V + pa.wide_W - 1) / pa.wide_W;
         // slices per tile: balanced over enough slice tiles for the team
         const int want_tt = std::max(ntt64, (pa.inner + nsi - 1) / nsi);
         pa.ns_tile = std::min(tc::kWSlices, (v.Nt + want_tt - 1) / want_tt);

@@ -48,6 +48,21 @@ def test_team_candidates_and_plan():
     assert all(team == inner == 4 for team, inner, _, _ in c)
     assert not any(m == 3 for *_, m in c)                          # V = 288: no CUDA-core mode
     assert (4, 4, 8, 3) in autotune.team_candidates(hmc.Params(L=6, Nt=32, beta=4.0), 4)
-    est = [10.0, 1.0, 1.0, 1.0, 0.5, 0.5]                        # ideal makespan 14 / 4 = 3.5
-    assert autotune.plan_teams(est, 4) == [True, False, False, False, False, False]
-    assert autotune.plan_teams([1.0] * 8, 4) == [False] * 8       # balanced: no teams
+    # one long chain: as a team of 4 (3.0) it no longer sets the makespan
+    est = [10.0] + [1.0] * 8
+    team = [3.0] + [None] * 8
+    assert autotune.plan_teams(est, team, 8, 4) == [True] + [False] * 8
+    assert autotune.simulate_batch(est, team, [True] + [False] * 8, 8, 4) == 3.0
+    assert autotune.simulate_batch(est, team, [False] * 9, 8, 4) == 10.0
+    assert autotune.plan_teams([1.0] * 8, [0.4] * 8, 8, 4) == [False] * 8   # balanced: none
+    # more team chains than clusters pay a second wave: 6 teams on 4 clusters
+    # end at 6.0, the best choice here; the planner takes the k with the
+    # smallest simulated makespan
+    est = [8.0] * 6 + [1.0] * 8
+    team = [3.0] * 6 + [None] * 8
+    flags = autotune.plan_teams(est, team, 16, 4)
+    m = autotune.simulate_batch(est, team, flags, 16, 4)
+    assert m == min(autotune.simulate_batch(est, team, [i < k for i in range(14)], 16, 4)
+                    for k in range(7)) == 6.0
+    # a slow team (6.0 of 8.0) does not pay for its second wave
+    assert autotune.plan_teams([8.0] * 6, [6.0] * 6, 16, 4) == [False] * 6

@@ -238,6 +238,9 @@ __global__ void __launch_bounds__(kSplitThreads)
     extern __shared__ float2 u_s[];
     __shared__ float s_max[kSplitThreads / 32];
     __shared__ int s_e;
+    // the application kernel may start its set-up now (programmatic
+    // dependent launch); it waits for this grid before reading B
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int t = blockIdx.x;
     const int ts = DAG ? (t + 1 == Nt ? 0 : t + 1) : (t == 0 ? Nt - 1 : t - 1);
     float mx = 0.f;
@@ -303,6 +306,9 @@ __global__ void __launch_bounds__(NTHR, 1)
     int i0, t0, ns;
     tile_coords(blockIdx.x, nti, ns_tile, c.Nt, i0, t0, ns);
     SrcSplit src{&bhi, &blo, inv};
+    // launched as a programmatic dependent of the split: the set-up above
+    // overlaps it; its B, scales and phase table are visible after this
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     tc_tile<DAG>(st, &mhi, &mlo, c.V, c.Nt, c.Vp, i0, t0, ns, src, 1.f, 1.f, epi);
     tc_teardown(st);
 }
@@ -332,6 +338,7 @@ __global__ void __launch_bounds__(NTHR, 1)
     const int ns = min(ns_tile, c.Nt - t0);
     const int kc0 = nk * rank / csplit, kc1 = nk * (rank + 1) / csplit;
     SrcSplitW src{&uhi, &ulo, inv, wide_u_rows(ns_tile)};
+    asm volatile("griddepcontrol.wait;" ::: "memory");   // the split (see k_apply)
     tc_wstage<DAG>(st, g, &mhi, &mlo, c.V, c.Nt, i0, t0, ns, kc0, kc1, src, 1.f);
     cluster_barrier_all();   // every member's partial staged (release / acquire)
     if (*((volatile int*)c.status) == 0)
@@ -1221,6 +1228,29 @@ void tc_ctx_free(hmc_ctx* c) {
     c->tc = nullptr;
 }
 
+// Launch an application kernel as a programmatic dependent of the split
+// that precedes it on the stream (its set-up overlaps the split; it waits
+// with griddepcontrol.wait before reading the split's output), in clusters
+// of `cluster` CTAs when cluster > 1.
+static int launch_dependent(const void* fn, int grid, int cluster, void** args,
+                            cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(tc::NTHR);
+    cfg.dynamicSmemBytes = tc::kSmemBytes;
+    cfg.stream = s;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    at[1].id = cudaLaunchAttributeClusterDimension;
+    at[1].val.clusterDim.x = (unsigned)cluster;
+    at[1].val.clusterDim.y = 1;
+    at[1].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = cluster > 1 ? 2 : 1;
+    return cudaLaunchKernelExC(&cfg, fn, args) == cudaSuccess ? HMC_OK : HMC_ERR_CUDA;
+}
+
 int tc_apply(hmc_ctx* c, const double* phi, const float2* in, float2* out, bool dag,
              cudaStream_t s) {
     const ChainView& v = c->view;
@@ -1242,36 +1272,26 @@ int tc_apply(hmc_ctx* c, const double* phi, const float2* in, float2* out, bool 
         const float* invp = t->inv_col;
         void* args[] = {&t->map_whi, &t->map_wlo, &t->map_uhi, &t->map_ulo, &vv,
                         &W, &ns, &cs, &inp, &outp, &invp};
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(tiles * cs);
-        cfg.blockDim = dim3(tc::NTHR);
-        cfg.dynamicSmemBytes = tc::kSmemBytes;
-        cfg.stream = s;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = (unsigned)cs;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = cs > 1 ? 1 : 0;
-        const void* fn = dag ? (const void*)tc::k_apply_w<true> : (const void*)tc::k_apply_w<false>;
-        return cudaLaunchKernelExC(&cfg, fn, args) == cudaSuccess ? HMC_OK : HMC_ERR_CUDA;
+        return launch_dependent(
+            dag ? (const void*)tc::k_apply_w<true> : (const void*)tc::k_apply_w<false>,
+            tiles * cs, cs, args, s);
     }
-    const int ns = c->tc->ns_apply;
+    int ns = c->tc->ns_apply;
     const int tiles = (v.Vr / tc::TM) * ((v.Nt + ns - 1) / ns);
-    if (dag) {
-        tc::k_split<true, false><<<v.Nt, tc::kSplitThreads, split_smem, s>>>(phi, in, v.cis_f, t->bhi, t->blo,
-                                                               t->inv_col, v.V, v.Vp, v.Nt);
-        tc::k_apply<true><<<tiles, tc::NTHR, tc::kSmemBytes, s>>>(
-            t->map_hi, t->map_lo, t->map_bhi, t->map_blo, v, ns, in, out, t->inv_col);
-    } else {
-        tc::k_split<false, false><<<v.Nt, tc::kSplitThreads, split_smem, s>>>(phi, in, v.cis_f, t->bhi,
-                                                                t->blo, t->inv_col, v.V, v.Vp,
-                                                                v.Nt);
-        tc::k_apply<false><<<tiles, tc::NTHR, tc::kSmemBytes, s>>>(
-            t->map_hi, t->map_lo, t->map_bhi, t->map_blo, v, ns, in, out, t->inv_col);
-    }
-    return cudaGetLastError() == cudaSuccess ? HMC_OK : HMC_ERR_CUDA;
+    if (dag)
+        tc::k_split<true, false><<<v.Nt, tc::kSplitThreads, split_smem, s>>>(
+            phi, in, v.cis_f, t->bhi, t->blo, t->inv_col, v.V, v.Vp, v.Nt);
+    else
+        tc::k_split<false, false><<<v.Nt, tc::kSplitThreads, split_smem, s>>>(
+            phi, in, v.cis_f, t->bhi, t->blo, t->inv_col, v.V, v.Vp, v.Nt);
+    if (cudaGetLastError() != cudaSuccess) return HMC_ERR_CUDA;
+    ChainView vv = v;
+    const float2* inp = in;
+    float2* outp = out;
+    const float* invp = t->inv_col;
+    void* args[] = {&t->map_hi, &t->map_lo, &t->map_bhi, &t->map_blo, &vv, &ns, &inp, &outp, &invp};
+    return launch_dependent(dag ? (const void*)tc::k_apply<true> : (const void*)tc::k_apply<false>,
+                            tiles, 1, args, s);
 }
 
 static int team_size(hmc_ctx* c, const void* kernel) {

@@ -81,6 +81,32 @@ struct EpiStore {
         out[(size_t)t * V + i] = r;
         acc = fmaf(r.x, r.x, fmaf(r.y, r.y, acc));
     }
+    // sites i, i+1 (i even) with 16-byte accesses
+    struct In2 {
+        float4 s, ph;
+    };
+    __device__ __forceinline__ In2 load2(int i, int t) const {
+        const size_t o = (size_t)t * V + i;
+        In2 v;
+        v.s = *reinterpret_cast<const float4*>(in + o);
+        v.ph = DAG ? *reinterpret_cast<const float4*>(cis + o) : make_float4(1.f, 0.f, 1.f, 0.f);
+        return v;
+    }
+    __device__ __forceinline__ void store2(int i, int t, const In2& v, float2 w0, float2 w1) {
+        float sg;
+        if (DAG) {
+            sg = (t == Nt - 1) ? -1.f : 1.f;
+            w0 = cmulcf(make_float2(v.ph.x, v.ph.y), w0);
+            w1 = cmulcf(make_float2(v.ph.z, v.ph.w), w1);
+        } else {
+            sg = (t == 0) ? -1.f : 1.f;
+        }
+        const float4 r = make_float4(v.s.x - sg * w0.x, v.s.y - sg * w0.y, v.s.z - sg * w1.x,
+                                     v.s.w - sg * w1.y);
+        *reinterpret_cast<float4*>(out + (size_t)t * V + i) = r;
+        acc = fmaf(r.x, r.x, fmaf(r.y, r.y, acc));
+        acc = fmaf(r.z, r.z, fmaf(r.w, r.w, acc));
+    }
 };
 
 // M q -> Ap; x_f += alpha p; r_f -= alpha Ap; accumulates |r_f|^2.
@@ -116,6 +142,32 @@ struct EpiCgUpdate {
         x[o] = xv;
         r[o] = rv;
         acc = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, acc));
+    }
+    struct In2 {
+        float4 q, p, x, r;
+    };
+    __device__ __forceinline__ In2 load2(int i, int t) const {
+        const size_t o = (size_t)t * V + i;
+        In2 v;
+        v.q = *reinterpret_cast<const float4*>(q + o);
+        v.p = *reinterpret_cast<const float4*>(p + o);
+        v.x = *reinterpret_cast<const float4*>(x + o);
+        v.r = *reinterpret_cast<const float4*>(r + o);
+        return v;
+    }
+    __device__ __forceinline__ void store2(int i, int t, const In2& v, float2 w0, float2 w1) {
+        const size_t o = (size_t)t * V + i;
+        const float sg = (t == 0) ? -1.f : 1.f;
+        const float4 ap = make_float4(v.q.x - sg * w0.x, v.q.y - sg * w0.y, v.q.z - sg * w1.x,
+                                      v.q.w - sg * w1.y);
+        const float4 xv = make_float4(fmaf(alpha, v.p.x, v.x.x), fmaf(alpha, v.p.y, v.x.y),
+                                      fmaf(alpha, v.p.z, v.x.z), fmaf(alpha, v.p.w, v.x.w));
+        const float4 rv = make_float4(fmaf(-alpha, ap.x, v.r.x), fmaf(-alpha, ap.y, v.r.y),
+                                      fmaf(-alpha, ap.z, v.r.z), fmaf(-alpha, ap.w, v.r.w));
+        *reinterpret_cast<float4*>(x + o) = xv;
+        *reinterpret_cast<float4*>(r + o) = rv;
+        acc = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, acc));
+        acc = fmaf(rv.z, rv.z, fmaf(rv.w, rv.w, acc));
     }
 };
 
@@ -157,6 +209,37 @@ struct EpiDirection {
         const float2 qv = make_float2(pv.x - sg * w.x, pv.y - sg * w.y);
         q[o] = qv;
         acc = fmaf(qv.x, qv.x, fmaf(qv.y, qv.y, acc));
+    }
+    struct In2 {
+        float4 r, p, ph;
+    };
+    __device__ __forceinline__ In2 load2(int i, int t) const {
+        const size_t o = (size_t)t * d.V + i;
+        In2 v;
+        if (d.refresh) {
+            const double2 a = d.r64[o], b = d.r64[o + 1];
+            v.r = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+        } else {
+            v.r = *reinterpret_cast<const float4*>(d.r + o);
+        }
+        v.p = *reinterpret_cast<const float4*>(d.p_old + o);
+        v.ph = *reinterpret_cast<const float4*>(cis + o);
+        return v;
+    }
+    __device__ __forceinline__ void store2(int i, int t, const In2& v, float2 w0, float2 w1) {
+        const size_t o = (size_t)t * d.V + i;
+        const float4 pv = make_float4(fmaf(d.beta, v.p.x, v.r.x), fmaf(d.beta, v.p.y, v.r.y),
+                                      fmaf(d.beta, v.p.z, v.r.z), fmaf(d.beta, v.p.w, v.r.w));
+        if (d.refresh) *reinterpret_cast<float4*>(r_out + o) = v.r;
+        *reinterpret_cast<float4*>(p_new + o) = pv;
+        const float sg = (t == Nt - 1) ? -1.f : 1.f;
+        w0 = cmulcf(make_float2(v.ph.x, v.ph.y), w0);
+        w1 = cmulcf(make_float2(v.ph.z, v.ph.w), w1);
+        const float4 qv = make_float4(pv.x - sg * w0.x, pv.y - sg * w0.y, pv.z - sg * w1.x,
+                                      pv.w - sg * w1.y);
+        *reinterpret_cast<float4*>(q + o) = qv;
+        acc = fmaf(qv.x, qv.x, fmaf(qv.y, qv.y, acc));
+        acc = fmaf(qv.z, qv.z, fmaf(qv.w, qv.w, acc));
     }
 };
 

@@ -289,14 +289,16 @@ __device__ bool tc_wstage(TcState& st, const WideGeom& g, const CUtensorMap* mhi
     return ok;
 }
 
-// Epilogue of a slice-major tile from staged accumulators: segments of 32
-// sites of one slice, dealt to the warps with the lanes along the sites
-// (the epilogue's global traffic is contiguous over each warp), UN of them
-// in flight per warp.  With csize > 1 the tile's K was split over the
-// csize CTAs of a thread-block cluster: this CTA (cluster rank `rank`)
-// takes its share of the segments and sums the csize staged partials
-// through distributed shared memory in rank order (deterministic); the
-// caller brackets it with cluster barriers.
+// Epilogue of a slice-major tile from staged accumulators: segments of 64
+// sites of one slice, dealt to the warps with the lanes along the sites, two
+// sites per lane (Epi::load2 / store2: 16-byte accesses, so the epilogue's
+// global traffic is contiguous over each warp in half the instructions),
+// UN segments in flight per warp.  V and i0 are even, so a pair never
+// straddles V.  With csize > 1 the tile's K was split over the csize CTAs of
+// a thread-block cluster: this CTA (cluster rank `rank`) takes its share of
+// the segments and sums the csize staged partials through distributed
+// shared memory in rank order (deterministic); the caller brackets it with
+// cluster barriers.
 template <class Src, class Epi>
 __device__ void tc_wepilogue(const TcState& st, int W, int V, int i0, int t0, int ns,
                              const Src& src, float inv_scale, float e_inv, Epi& epi, int rank,
@@ -305,36 +307,36 @@ __device__ void tc_wepilogue(const TcState& st, int W, int V, int i0, int t0, in
     const int rs = wide_row_floats(W);
     const float* ds = reinterpret_cast<const float*>(st.base);
     const uint32_t ds_s = smem_u32(ds);
-    using In = typename Epi::In;
-    constexpr int UN = 3;
-    const int nseg = (W + 31) / 32, total = ns * nseg;
+    using In2 = typename Epi::In2;
+    constexpr int UN = 2;
+    const int nseg = (W + 63) / 64, total = ns * nseg;
     const int s0 = (int)((long long)total * rank / csize);
     const int s1 = (int)((long long)total * (rank + 1) / csize);
     for (int base = s0 + warp; base < s1; base += UN * (NTHR / 32)) {
-        In in[UN];
+        In2 in[UN];
 #pragma unroll
         for (int u = 0; u < UN; ++u) {
             const int sg = base + u * (NTHR / 32);
-            const int tt = sg / nseg, n = (sg - tt * nseg) * 32 + lane;
-            if (sg < s1 && n < W && i0 + n < V) in[u] = epi.load(i0 + n, t0 + tt);
+            const int tt = sg / nseg, n = (sg - tt * nseg) * 64 + 2 * lane;
+            if (sg < s1 && n < W && i0 + n < V) in[u] = epi.load2(i0 + n, t0 + tt);
         }
 #pragma unroll
         for (int u = 0; u < UN; ++u) {
             const int sg = base + u * (NTHR / 32);
-            const int tt = sg / nseg, n = (sg - tt * nseg) * 32 + lane;
+            const int tt = sg / nseg, n = (sg - tt * nseg) * 64 + 2 * lane;
             if (sg < s1 && n < W && i0 + n < V) {
                 float is = inv_scale * e_inv;
                 if constexpr (Src::kTma) is = src.inv[t0 + tt] * e_inv;
-                float2 d;
+                float4 d;
                 if (csize == 1) {
-                    d = reinterpret_cast<const float2*>(ds + tt * rs)[n];
+                    d = *reinterpret_cast<const float4*>(ds + tt * rs + 2 * n);
                 } else {
-                    d = make_float2(0.f, 0.f);
+                    d = make_float4(0.f, 0.f, 0.f, 0.f);
                     const uint32_t off = ds_s + (uint32_t)((tt * rs + 2 * n) * 4);
                     // non-volatile loads (the sums may trail them, so the
                     // members' loads can be in flight together); the memory
                     // clobber keeps them after the caller's cluster barrier
-                    float x[kMaxClusterW], y[kMaxClusterW];
+                    float4 x[kMaxClusterW];
 #pragma unroll
                     for (int qr = 0; qr < kMaxClusterW; ++qr) {
                         if (qr < csize) {
@@ -342,8 +344,8 @@ __device__ void tc_wepilogue(const TcState& st, int W, int V, int i0, int t0, in
                             asm("mapa.shared::cluster.u32 %0, %1, %2;"
                                 : "=r"(ra)
                                 : "r"(off), "r"(qr));
-                            asm("ld.shared::cluster.v2.f32 {%0, %1}, [%2];"
-                                : "=f"(x[qr]), "=f"(y[qr])
+                            asm("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                                : "=f"(x[qr].x), "=f"(x[qr].y), "=f"(x[qr].z), "=f"(x[qr].w)
                                 : "r"(ra)
                                 : "memory");
                         }
@@ -351,12 +353,15 @@ __device__ void tc_wepilogue(const TcState& st, int W, int V, int i0, int t0, in
 #pragma unroll
                     for (int qr = 0; qr < kMaxClusterW; ++qr) {
                         if (qr < csize) {
-                            d.x += x[qr];
-                            d.y += y[qr];
+                            d.x += x[qr].x;
+                            d.y += x[qr].y;
+                            d.z += x[qr].z;
+                            d.w += x[qr].w;
                         }
                     }
                 }
-                epi.store(i0 + n, t0 + tt, in[u], make_float2(d.x * is, d.y * is));
+                epi.store2(i0 + n, t0 + tt, in[u], make_float2(d.x * is, d.y * is),
+                           make_float2(d.z * is, d.w * is));
             }
         }
     }

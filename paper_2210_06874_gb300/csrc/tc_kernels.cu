@@ -549,7 +549,7 @@ template <int KIND>
 __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& sm64,
                          const CUtensorMap* mhi, const CUtensorMap* mlo,
                          const PersistentArgs& pa, ClusterSync* ics, const double2* chi,
-                         double2* x64, MixedResult& res) {
+                         double2* x64, MixedResult& res, bool warm = false) {
     constexpr bool SMALL = KIND == kKindSmall;
     float2 *rf = c.r_f, *pf = c.p_f, *pn = c.p2_f, *qf = c.q_f, *xf = c.x_f;
     const int inner_size = min(max(pa.inner, 1), tm.size);
@@ -563,7 +563,7 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
     double v1[1] = {0.0};
     HMC_TEAM_ELEMS(e, c, tm) {
         const double2 ch = chi[e];
-        x64[e] = make_double2(0.0, 0.0);
+        if (!warm) x64[e] = make_double2(0.0, 0.0);
         v1[0] += ch.x * ch.x + ch.y * ch.y;
     }
     if (!team_sum<1>(tm, v1)) return false;
@@ -576,6 +576,25 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
         if (!finite_d(chi2)) res.status = HMC_ERR_NONFINITE;
         return true;
     }
+    const double stop = pa.tol * pa.tol * chi2;
+    // warm start (a later solve of a trajectory: same chi, the field moved by
+    // one MD step): the FP64 true residual of the given x64 is the starting
+    // residual of the FP32 iteration
+    double rr_true = chi2;
+    const double2* r0 = chi;
+    if (warm) {
+        if (!f64_residual(c, tm, sm64, chi, x64, rr_true)) return false;
+        ++res.reliable_updates;
+        if (!finite_d(rr_true)) {
+            res.status = HMC_ERR_NONFINITE;
+            return true;
+        }
+        if (rr_true <= stop) {
+            res.true_res = sqrt(rr_true / chi2);
+            return true;
+        }
+        r0 = c.r;
+    }
     // FP32 iterates on the inner team (their owners).  A chain solved by one
     // CTA with E resident keeps them in shared memory: r, p, p', q, x and the
     // FP32 phase table, six vectors after the B ring.
@@ -586,7 +605,7 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
       if (in_inner) {
         // small lattice: FP32 iterates of the cluster's slices in shared memory
         small_init_view(sm, st.base, tm.rank, inner_size, c.V, c.Nt);
-        double v2[1] = {small_setup(sm, c, chi)};
+        double v2[1] = {small_setup(sm, c, r0)};
         if (!team_sum<1>(ti, v2)) return false;
         rr = v2[0];
       }
@@ -610,7 +629,7 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
         }
         double v2[1] = {0.0};
         HMC_TEAM_ELEMS(e, c, ti) {
-            const double2 ch = chi[e];
+            const double2 ch = r0[e];
             const float2 rv = make_float2((float)ch.x, (float)ch.y);
             rf[e] = rv;
             pf[e] = make_float2(0.f, 0.f);
@@ -621,9 +640,7 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
         rr = v2[0];
     }
     __shared__ CgScalars s_cg;
-    double rr_true = chi2;
     bool refresh = false;
-    const double stop = pa.tol * pa.tol * chi2;
     if (threadIdx.x == 0) {
         s_cg.rr = (float)rr;
         s_cg.pp = (float)rr;
@@ -903,7 +920,10 @@ __device__ bool run_trajectory(const ChainView& c, Team& tm, TcState& st, f64::S
             if (!(ok = team_barrier(tm))) break;
         }
         MixedResult res{};
-        if (!(ok = cg_mixed<KIND>(c, tm, st, sm64, mhi, mlo, pa, ics, c.chi, c.x, res))) break;
+        // later solves start from the previous solution (chronological
+        // initial guess); the first from zero
+        if (!(ok = cg_mixed<KIND>(c, tm, st, sm64, mhi, mlo, pa, ics, c.chi, c.x, res, step > 0)))
+            break;
         iters += res.iterations;
         rus += res.reliable_updates;
         ++solves;

@@ -200,7 +200,6 @@ __device__ bool tc_wstage(TcState& st, const WideGeom& g, const CUtensorMap* mhi
             const uint32_t idesc = idesc_f16(WM, Wm);
             const uint32_t tmem = bars.tmem_base;
             for (int j = 0; j < nk && ok; ++j) {
-                const int kc = kc0 + j;
                 const uint32_t s = (uint32_t)j % S, n = use0[s] + (uint32_t)j / S;
                 ok = mbar_wait(smem_u32(&bars.wfull[s]), n & 1, st.status);
                 if (!ok) break;

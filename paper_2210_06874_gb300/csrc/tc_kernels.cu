@@ -907,6 +907,11 @@ __device__ bool run_trajectory(const ChainView& c, Team& tm, TcState& st, f64::S
     const double ed = a.eps * c.delta;
     const double edrift = md_drift(a) * ed;
     const int n_stages = md_stages(a);
+    // initial guesses of the solves (the solves sit at equally spaced fields):
+    // the first from zero, the second from the first solution, later ones
+    // from the linear extrapolation 2 x_{k-1} - x_{k-2}; rho, free once chi
+    // and H0 are formed, keeps x_{k-2}
+    double2* xold = c.rho;
     for (int step = 0; ok && step <= n_stages; ++step) {
         if (step > 0) {
             HMC_TEAM_ELEMS(e, c, tm) {
@@ -916,12 +921,16 @@ __device__ bool run_trajectory(const ChainView& c, Team& tm, TcState& st, f64::S
                 sincos(ph, &s, &co);
                 c.cis[e] = make_double2(co, s);
                 c.cis_f[e] = make_float2((float)co, (float)s);
+                const double2 x1 = c.x[e];
+                if (step > 1) {
+                    const double2 x2 = xold[e];
+                    c.x[e] = make_double2(2.0 * x1.x - x2.x, 2.0 * x1.y - x2.y);
+                }
+                xold[e] = x1;
             }
             if (!(ok = team_barrier(tm))) break;
         }
         MixedResult res{};
-        // later solves start from the previous solution (chronological
-        // initial guess); the first from zero
         if (!(ok = cg_mixed<KIND>(c, tm, st, sm64, mhi, mlo, pa, ics, c.chi, c.x, res, step > 0)))
             break;
         iters += res.iterations;

@@ -205,6 +205,7 @@ int hmc_ctx_create(const hmc_params* p, hmc_ctx** out) {
     v.q = (double2*)ctx_alloc(c, N * sizeof(double2), &ok);
     v.chi = (double2*)ctx_alloc(c, N * sizeof(double2), &ok);
     v.rho = (double2*)ctx_alloc(c, N * sizeof(double2), &ok);
+    v.xh = (double2*)ctx_alloc(c, N * sizeof(double2), &ok);
     v.pi = (double*)ctx_alloc(c, N * sizeof(double), &ok);
     v.phi_old = (double*)ctx_alloc(c, N * sizeof(double), &ok);
     v.bar = (unsigned*)ctx_alloc(c, 8 * sizeof(unsigned), &ok);

@@ -27,6 +27,7 @@ struct ChainView {
     // FP64 workspaces, double2 [Nt][V] each
     double2 *cis;               // exp(i phi)
     double2 *x, *r, *p, *q, *chi, *rho;
+    double2 *xh;                // solution history for the mixed trajectory's guesses
     double *pi, *phi_old;       // double [Nt][V]
     // FP32 workspaces for the mixed path, float2 [Nt][V] each
     float2 *cis_f, *r_f, *p_f, *p2_f, *q_f, *x_f;

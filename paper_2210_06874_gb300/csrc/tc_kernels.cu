@@ -908,9 +908,10 @@ __device__ bool run_trajectory(const ChainView& c, Team& tm, TcState& st, f64::S
     const double edrift = md_drift(a) * ed;
     const int n_stages = md_stages(a);
     // initial guesses of the solves (the solves sit at equally spaced fields):
-    // the first from zero, the second from the first solution, later ones
-    // from the linear extrapolation 2 x_{k-1} - x_{k-2}; rho, free once chi
-    // and H0 are formed, keeps x_{k-2}
+    // the first from zero, the second from the first solution, the third
+    // from the linear extrapolation 2 x_{k-1} - x_{k-2}, later ones from the
+    // quadratic one 3 x_{k-1} - 3 x_{k-2} + x_{k-3}; rho, free once chi and
+    // H0 are formed, keeps x_{k-2}, xh keeps x_{k-3}
     double2* xold = c.rho;
     for (int step = 0; ok && step <= n_stages; ++step) {
         if (step > 0) {
@@ -922,9 +923,14 @@ __device__ bool run_trajectory(const ChainView& c, Team& tm, TcState& st, f64::S
                 c.cis[e] = make_double2(co, s);
                 c.cis_f[e] = make_float2((float)co, (float)s);
                 const double2 x1 = c.x[e];
-                if (step > 1) {
+                if (step > 2) {
+                    const double2 x2 = xold[e], x3 = c.xh[e];
+                    c.x[e] = make_double2(3.0 * (x1.x - x2.x) + x3.x, 3.0 * (x1.y - x2.y) + x3.y);
+                    c.xh[e] = x2;
+                } else if (step > 1) {
                     const double2 x2 = xold[e];
                     c.x[e] = make_double2(2.0 * x1.x - x2.x, 2.0 * x1.y - x2.y);
+                    c.xh[e] = x2;
                 }
                 xold[e] = x1;
             }

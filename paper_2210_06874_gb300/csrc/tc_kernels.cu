@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(NTHR, 1)
     const int nti = c.Vr / TM;
     int i0, t0, ns;
     tile_coords(blockIdx.x, nti, ns_tile, c.Nt, i0, t0, ns);
-    SrcSplit src{&bhi, &blo, inv};
+    SrcSplit src{&bhi, &blo, inv, ((2 * ns_tile + 15) / 16) * 16};
     // launched as a programmatic dependent of the split: the set-up above
     // overlaps it; its B, scales and phase table are visible after this
     asm volatile("griddepcontrol.wait;" ::: "memory");

@@ -222,6 +222,7 @@ struct SrcSplit {
     const CUtensorMap* bhi;
     const CUtensorMap* blo;
     const float* inv;
+    int rows;     // TMA box rows of B (the MMA N of every tile, the last ragged one too)
 };
 
 // Fill the B operand of K chunk [k0, k0+64) for the tile's slices t0..t0+ns-1
@@ -452,7 +453,10 @@ __device__ bool tc_tile(TcState& st, const CUtensorMap* mhi, const CUtensorMap* 
     TileBars& bars = *st.bars;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = Vp / KCH;
-    const int N = ((2 * ns + 15) / 16) * 16;
+    // MMA N: 2 x slices rounded up to 16; with B loaded by TMA, the box
+    // height, so the expected bytes match the copy on a ragged last tile
+    int N = ((2 * ns + 15) / 16) * 16;
+    if constexpr (Src::kTma) N = src.rows;
     const int S = st.stages;
     const bool streaming = st.mode == kStreaming;
     const uint32_t g0 = st.gchunk;

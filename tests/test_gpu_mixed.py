@@ -140,3 +140,20 @@ def test_trajectory_mixed_deterministic():
     o1 = [c.trajectory(a, 3, t).dH for t in range(2)]
     o2 = [c.trajectory(b, 3, t).dH for t in range(2)]
     assert o1 == o2 and torch.equal(a, b)
+
+
+@pytest.mark.parametrize("L,Nt,ns", [(5, 13, 16), (6, 40, 32), (3, 20, 32), (9, 21, 16)])
+def test_apply_mixed_ragged_last_tile(L, Nt, ns):
+    """Standalone applications with 16 or 32 slices per tile and a ragged
+    last tile (fewer slices, same TMA box for the pre-split operand)."""
+    beta, U = 0.125 * Nt, 3.0
+    V = 2 * L * L
+    c = hmc.Context(hmc.Params(L=L, Nt=Nt, beta=beta, U=U, tile_slices=ns))
+    E = oracle_E(L, Nt, beta)
+    phi = synth.gaussian_field(L * 7 + Nt, Nt, V, beta / Nt * U)
+    psi = dev(synth.complex_gaussian(L * 11 + Nt, Nt, V), torch.complex64)
+    psi_in = psi.cpu().numpy().astype(np.complex128)
+    for dag, op in ((False, ops.apply_M), (True, ops.apply_Mdag)):
+        fn = c.apply_Mdag if dag else c.apply_M
+        got = fn(dev(phi), psi, prec=hmc.PREC_MIXED).cpu().numpy()
+        assert rel(got, op(E, phi, psi_in)) < APPLY_TOL

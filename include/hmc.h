@@ -124,6 +124,13 @@ typedef struct hmc_params {
                             Mryglod and Folk (2003), lambda = 0.19318...
                             (n_md steps, 2 n_md + 1 force evaluations, a
                             much smaller energy violation at equal step) */
+    double mu;           /* chemical potential (the sign-problem setting of
+                            the paper's section on tensor networks, where
+                            p ~ det(M[phi,mu] M[phi,-mu]^dag)): taken into
+                            the hopping exponent, E = exp(delta (kappa h +
+                            mu)) = e^{delta mu} exp(delta kappa h), in every
+                            operator of the context (not in the Eq. (2.2)
+                            operator of hmc_apply_brs); 0 = half filling */
 } hmc_params;
 
 typedef struct hmc_cg_stats {

@@ -29,11 +29,14 @@ from . import lattice
 # ---------------------------------------------------------------------------
 # transfer matrix
 # ---------------------------------------------------------------------------
-def transfer_matrix(h, delta_kappa):
-    """E = exp(delta*kappa*h) through the eigendecomposition of the real
-    symmetric h: E = Q diag(exp(delta*kappa*w)) Q^T."""
+def transfer_matrix(h, delta_kappa, delta_mu=0.0):
+    """E = exp(delta*kappa*h + delta*mu) through the eigendecomposition of
+    the real symmetric h: E = Q diag(exp(delta*kappa*w + delta*mu)) Q^T.
+    The chemical potential mu (the sign-problem setting of the paper's
+    tensor-network section, p ~ det(M[phi,mu] M[phi,-mu]^dag)) enters the
+    hopping exponent; delta_mu = 0 is half filling."""
     w, Q = np.linalg.eigh(h)
-    return (Q * np.exp(delta_kappa * w)) @ Q.T
+    return (Q * np.exp(delta_kappa * w + delta_mu)) @ Q.T
 
 
 def time_signs(Nt):

@@ -143,6 +143,8 @@ static int valid_params(const hmc_params* p) {
     if (p->operand_mode < 0 || p->operand_mode > 4) return 0;
     if (p->cluster_mode < 0 || p->cluster_mode > 2) return 0;
     if (p->integrator < 0 || p->integrator > 1) return 0;
+    // |delta mu| <= 5: the scaled E keeps its FP16 split in range
+    if (!std::isfinite(p->mu) || std::fabs(p->mu * p->beta / p->Nt) > 5.0) return 0;
     if (p->operand_mode == 4) {
         if (p->tile_slices < 0 || p->tile_slices > 64) return 0;
     } else if (p->tile_slices != 0 && p->tile_slices != 8 && p->tile_slices != 16 &&
@@ -195,6 +197,11 @@ int hmc_ctx_create(const hmc_params* p, hmc_ctx** out) {
     v.U = p->U;
     std::vector<double> E;
     build_transfer_matrix(p->L, v.delta * p->kappa, E);
+    if (p->mu != 0.0) {
+        // chemical potential in the hopping exponent: exp(delta (kappa h + mu))
+        const double f = std::exp(v.delta * p->mu);
+        for (double& e : E) e *= f;
+    }
     bool ok = true;
     const size_t N = (size_t)v.N;
     double* dE = (double*)ctx_alloc(c, E.size() * sizeof(double), &ok);

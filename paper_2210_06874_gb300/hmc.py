@@ -49,7 +49,7 @@ class hmc_params(ctypes.Structure):
                 ("ru_delta", ctypes.c_double), ("team_ctas", ctypes.c_int),
                 ("tile_slices", ctypes.c_int), ("inner_ctas", ctypes.c_int),
                 ("operand_mode", ctypes.c_int), ("cluster_mode", ctypes.c_int),
-                ("integrator", ctypes.c_int)]
+                ("integrator", ctypes.c_int), ("mu", ctypes.c_double)]
 
 
 class hmc_cg_stats(ctypes.Structure):
@@ -149,6 +149,7 @@ class Params:
     operand_mode: int = 0
     cluster_mode: int = 0
     integrator: int = 0
+    mu: float = 0.0
 
     @property
     def V(self):
@@ -163,7 +164,7 @@ class Params:
                           self.traj_length, self.cg_tol, self.cg_max_iter, self.precision,
                           self.ru_delta, self.team_ctas, self.tile_slices,
                           self.inner_ctas, self.operand_mode, self.cluster_mode,
-                          self.integrator)
+                          self.integrator, self.mu)
 
 
 class Context:

@@ -53,7 +53,8 @@ def bad(**kw):
                                          ("precision", 7), ("ru_delta", 1.5),
                                          ("L", 30000), ("operand_mode", 5),
                                          ("cluster_mode", 3), ("cluster_mode", -1),
-                                         ("integrator", 2), ("integrator", -1)])
+                                         ("integrator", 2), ("integrator", -1),
+                                         ("mu", float("nan")), ("mu", 100.0)])
 def test_ctx_create_rejects_bad_params(lib, field, value):
     h = ctypes.c_void_p()
     p = bad(**{field: value})

@@ -175,3 +175,55 @@ def test_brs_adjoint_identity_large():
     lhs = np.vdot(u, ops.apply_M_brs(L, phi, v, 0.125, 1.0))
     rhs = np.vdot(ops.apply_Mdag_brs(L, phi, u, 0.125, 1.0), v)
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+# chemical potential (sign-problem setting, p ~ det(M[phi,mu] M[phi,-mu]^dag)):
+# mu enters the hopping exponent, E = exp(delta (kappa h + mu))
+
+@pytest.mark.parametrize("L,Nt,beta,kappa,mu", [(1, 4, 1.0, 1.0, 0.3), (2, 6, 2.0, 1.0, -0.5),
+                                                (3, 8, 2.0, 1.0, 0.7), (3, 5, 3.0, -0.7, 1.1)])
+def test_free_determinant_with_mu_closed_form(L, Nt, beta, kappa, mu):
+    """phi = 0: det M[0, mu] = prod over eigenvalues lam of h of
+    (1 + e^{beta (kappa lam + mu)}) -- the free grand-canonical partition
+    function of one species."""
+    delta = beta / Nt
+    E = ops.transfer_matrix(lattice.hopping_matrix(L), delta * kappa, delta * mu)
+    sign, logdet = np.linalg.slogdet(ops.dense_M(E, np.zeros((Nt, 2 * L * L))))
+    f = bloch_moduli(L)
+    lam = np.concatenate([f, -f])
+    want = np.sum(np.log1p(np.exp(beta * (kappa * lam + mu))))
+    assert abs(logdet - want) < 1e-11
+    assert abs(sign - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("L,Nt,mu", [(1, 4, 0.4), (2, 3, -0.9)])
+def test_kappa_zero_with_mu_closed_form(L, Nt, mu):
+    """kappa = 0: det M = prod_x (1 + e^{beta mu} e^{i sum_t phi_{x,t}})."""
+    rng = np.random.default_rng(16)
+    V = 2 * L * L
+    beta = 1.5
+    E = ops.transfer_matrix(lattice.hopping_matrix(L), 0.0, beta / Nt * mu)
+    phi = random_field(rng, Nt, V, 1.0)
+    want = np.prod(1.0 + np.exp(beta * mu) * np.exp(1j * phi.sum(axis=0)))
+    got = np.linalg.det(ops.dense_M(E, phi))
+    assert abs(got - want) <= 1e-12 * abs(want)
+
+
+def test_sign_problem_weight():
+    """det(M[phi,mu] M[phi,-mu]^dag) is real and positive at mu = 0 (it is
+    |det M|^2) and picks up a non-trivial phase at mu != 0."""
+    rng = np.random.default_rng(17)
+    L, Nt, delta = 2, 4, 0.25
+    V = 2 * L * L
+    h = lattice.hopping_matrix(L)
+    phi = random_field(rng, Nt, V, 1.0)
+
+    def weight(mu):
+        Mp = ops.dense_M(ops.transfer_matrix(h, delta, delta * mu), phi)
+        Mm = ops.dense_M(ops.transfer_matrix(h, delta, -delta * mu), phi)
+        return np.linalg.det(Mp) * np.conj(np.linalg.det(Mm))
+
+    w0 = weight(0.0)
+    assert abs(w0.imag) <= 1e-12 * abs(w0) and w0.real > 0
+    w1 = weight(0.8)
+    assert abs(np.angle(w1)) > 1e-3

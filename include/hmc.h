@@ -212,6 +212,18 @@ int hmc_action(hmc_ctx* ctx, const double* phi, const void* chi, const void* x, 
 int hmc_trajectory(hmc_ctx* ctx, double* phi, uint64_t seed, uint64_t traj_index,
                    uint32_t chain, hmc_traj_out* out, void* stream);
 
+/* ---- Observables (M^{-1} sources) ---------------------------------------
+ * Zero-momentum single-particle correlator on sublattice A, the correlator
+ * whose decay in Euclidean time gives the single-particle gap (§4): source
+ * b = V_A^{-1/2} on the A sites (x < V/2) of slice 0; g = M^{-1} b =
+ * M^dag (M M^dag)^{-1} b (CG to tol in `precision`, then the FP64 M^dag);
+ * C[t] = V_A^{-1/2} sum_{x < V/2} g_t(x), t = 0..Nt-1.  phi: device double
+ * [Nt][V]; C: device complex double [Nt]; stats as for hmc_cg_solve (and
+ * its status codes).  Allocates 3 V Nt complex doubles on `stream` for the
+ * call (stream-ordered).  The gap fit itself is analysis, not done here. */
+int hmc_correlator_k0(hmc_ctx* ctx, const double* phi, double tol, int max_iter, int precision,
+                      void* C, hmc_cg_stats* stats, void* stream);
+
 /* ---- The printed operator, Eq. (2.2) -------------------------------------
  * The mixed-differencing (Brower-Rebbi-Schaich) fermion operator exactly as
  * Eq. (2.2) prints it, as a sparse stencil; no context needed.  With

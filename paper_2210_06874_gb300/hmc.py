@@ -93,6 +93,8 @@ SIGNATURES = {
     "hmc_brs_phases": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
     "hmc_apply_brs": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P,
                                      ctypes.c_int, ctypes.c_int, _P]),
+    "hmc_correlator_k0": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                         _P, ctypes.POINTER(hmc_cg_stats), _P]),
     "hmc_cg_solve_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P,
                                             ctypes.c_double, ctypes.c_int,
                                             ctypes.POINTER(hmc_cg_stats), _P]),
@@ -242,6 +244,19 @@ class Context:
                                                      tol, max_iter, prec, ctypes.byref(st),
                                                      _stream()), allow)
         return x, st
+
+    def correlator_k0(self, phi, tol=None, max_iter=None, prec=PREC_FP64):
+        """Zero-momentum single-particle correlator on sublattice A,
+        C[t] (complex128 [Nt]) from one M^{-1} source (hmc_correlator_k0)."""
+        self._field(phi, "phi", torch.float64)
+        C = torch.empty(self.params.Nt, dtype=torch.complex128, device=phi.device)
+        st = hmc_cg_stats()
+        tol = self.params.cg_tol if tol is None else tol
+        max_iter = self.params.cg_max_iter if max_iter is None else max_iter
+        _check("hmc_correlator_k0",
+               self.lib.hmc_correlator_k0(self._h, _ptr(phi), tol, max_iter, prec, _ptr(C),
+                                          ctypes.byref(st), _stream()))
+        return C, st
 
     def force(self, phi, x, F=None):
         self._field(phi, "phi", torch.float64)

@@ -945,7 +945,18 @@ __device__ bool run_trajectory(const ChainView& c, Team& tm, TcState& st, f64::S
         max_res = fmax(max_res, res.true_res);
         if (res.status != HMC_OK && status == HMC_OK) status = res.status;
         ea.kick = md_kick(a, step) * ed;
-        f64::apply_team<true, f64::EPI_FORCE>(c, tm, c.x, nullptr, ea, sm64);
+        if (res.status == HMC_OK) {
+            // the solve ended on an FP64 true residual of its final x, which
+            // left q = M^dag x (same FP64 tile): the force needs no
+            // application of its own
+            HMC_TEAM_ELEMS(e, c, tm) {
+                const double2 xv = c.x[e], y = c.q[e];
+                const double f = phi[e] * inv_dU + 2.0 * (xv.y * y.x - xv.x * y.y);
+                c.pi[e] -= ea.kick * f;
+            }
+        } else {
+            f64::apply_team<true, f64::EPI_FORCE>(c, tm, c.x, nullptr, ea, sm64);
+        }
         ok = team_barrier(tm);
     }
     double h1[3] = {0.0, 0.0, 0.0};

@@ -364,8 +364,11 @@ __device__ inline void small_matvec(const SmallCg& sc, const float2* U) {
     const float4* U4 = reinterpret_cast<const float4*>(U);
     float2* W = sc.v(l.w);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const int G = l.Vr / 32;
-    for (int item = warp; item < G * l.KS; item += nw) {
+    const int G = l.Vr / 32, items = G * l.KS;
+    // with fewer items than warps the last warps take them: warp 0 is then
+    // still sending the partial norm of the epilogue before (small_sum_begin)
+    const int w0 = items < nw ? nw - items : 0;
+    for (int item = warp - w0; warp >= w0 && item < items; item += nw - w0) {
         const int g = item % G, h = item / G;
         const int i = g * 32 + lane;
         const int k0 = (h * l.V) / l.KS, k1 = ((h + 1) * l.V) / l.KS;

@@ -29,7 +29,7 @@ METRIC = ("HMC trajectories/s and M-applications/s (frac. of roofline), "
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # dram__bytes_read.sum + dram__bytes_write.sum of one trajectory launch in the
 # CUDA-core cluster mode, by (workload, cluster size), from ncu
-CAPTURED_TRAFFIC = {}
+CAPTURED_TRAFFIC = {("l6_nt32", 16): 764420}
 # FP32 FMA peak of the whole GPU from unit counts and the maximum SM clock
 FP32_FMA_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}

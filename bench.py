@@ -558,7 +558,7 @@ def run_apply(args):
 
 
 def run_batch(args):
-    """Config 4: many chains of uneven size, one persistent launch per
+    """Batched workload: many chains of uneven size, one persistent launch per
     trajectory of every chain (hmc_batch_trajectory); value = aggregate
     trajectories/s.  Also times the same chains as a loop of single-chain
     hmc_trajectory launches (each using the whole GPU)."""

@@ -16,7 +16,7 @@ hmc        CG on M M^dagger, action Eq. (2.1), force, leapfrog, Metropolis (§2)
 philox     Philox4x32-10 counter-based generator (Salmon et al., SC'11) and
            the Box-Muller normals drawn from it
 
-Conventions (readings of the paper; every one is listed in the design doc):
+Conventions (readings of the paper where it leaves a choice):
   * field phi is the product delta*phi_paper, so phases are exp(+i phi) and the
     bosonic action is sum(phi^2) / (2 delta U)
   * site index x = s*L*L + m1*L + m2 (s=0: sublattice A, s=1: sublattice B)

@@ -1,5 +1,5 @@
 """The adjoint force behind torch.autograd against the oracle gradient and
-central finite differences (workload of config 2: L=6, Nt=32, U=3.5, beta=4,
+central finite differences (the L=6, Nt=32, U=3.5, beta=4 workload,
 16 random fields)."""
 import numpy as np
 import pytest

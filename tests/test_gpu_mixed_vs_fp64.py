@@ -1,4 +1,4 @@
-"""Config 3: the mixed path against the plain FP64 GPU path on the same
+"""The mixed path against the plain FP64 GPU path on the same
 seeded trajectories (L=12, Nt=64, U=3.8, beta=8), with the differences in
 Delta H, the force and the CG solution stated and bounded."""
 import numpy as np

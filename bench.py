@@ -613,6 +613,27 @@ def run_batch(args):
         traj += 1
     clk = clocks.stop()
     value = world * n * args.steps / (total_ms * 1e-3)
+    # end to end through the public API with host buffers: every chain's
+    # field in from pinned host memory, one batched trajectory, the fields
+    # back (the per-chain records come back inside the call)
+    phi_host = torch.empty(b.total, dtype=torch.float64, pin_memory=True)
+    phi_host.copy_(phi.cpu())
+    back = torch.empty_like(phi_host)
+    torch.cuda.synchronize()
+    e2e_steps = max(2, min(args.steps, 3))
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    for _ in range(e2e_steps):
+        phi.copy_(phi_host, non_blocking=True)
+        b.trajectory(phi, seed, traj, allow_failure=True)
+        back.copy_(phi, non_blocking=True)
+        stream.synchronize()
+        phi_host.copy_(back)
+        traj += 1
+    e.record(stream)
+    e.synchronize()
+    e2e_value = world * n / (s.elapsed_time(e) / e2e_steps * 1e-3)
+    e2e_bytes = b.total * 8
     # loop of single-chain launches over the same chains (first K_loop chains)
     n_loop = min(n, args.loop_chains)
     loop_ms = 0.0
@@ -691,6 +712,9 @@ def run_batch(args):
         "cg_iterations_per_traj": statistics.mean(o.cg_iterations for o in outs),
         "max_true_residual": max(o.max_true_residual for o in outs),
         "statuses": sorted(set(o.status for o in outs)),
+        "e2e": {"value": e2e_value, "unit": "trajectories/s",
+                "h2d_bytes_per_step": e2e_bytes,
+                "d2h_bytes_per_step": e2e_bytes + n * 16 * 8},   # + 16 doubles per chain record
         "gpu_launches": args.steps,
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,

@@ -1671,8 +1671,9 @@ int tc_batch_create(const hmc_params* p, int n, TcBatch** out) {
     TcBatch* b = new TcBatch();
     b->n = n;
     int st = HMC_OK;
-    // one context per chain (workspaces); chains with the same lattice and
-    // delta*kappa share the first such context's E, its split and maps
+    // one context per chain (workspaces); chains with the same lattice,
+    // delta*kappa and delta*mu share the first such context's E, its splits
+    // and maps
     std::vector<int> leader(n);
     std::vector<int> map_slot(n);
     int n_maps = 0;
@@ -1685,7 +1686,8 @@ int tc_batch_create(const hmc_params* p, int n, TcBatch** out) {
         leader[i] = i;
         for (int j = 0; j < i; ++j)
             if (p[j].L == p[i].L &&
-                p[j].beta / p[j].Nt * p[j].kappa == p[i].beta / p[i].Nt * p[i].kappa) {
+                p[j].beta / p[j].Nt * p[j].kappa == p[i].beta / p[i].Nt * p[i].kappa &&
+                p[j].beta / p[j].Nt * p[j].mu == p[i].beta / p[i].Nt * p[i].mu) {
                 leader[i] = leader[j];
                 break;
             }

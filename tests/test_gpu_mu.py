@@ -81,3 +81,27 @@ def test_mixed_trajectory_with_mu_matches_oracle():
     assert abs(out.dH - want["dH"]) < 1e-7
     assert bool(out.accept) == want["accept"]
     assert rel(phi.cpu().numpy(), want["phi"]) < 1e-8
+
+
+def test_batch_chains_differing_only_in_mu():
+    """Chains of one lattice and delta*kappa but different mu must not share
+    the transfer matrix: each batch chain matches its own single-chain run."""
+    chains = [(6, 16, 0.0), (6, 16, 0.6), (6, 16, -0.6)]
+
+    def p(L, Nt, mu, **kw):
+        return hmc.Params(L=L, Nt=Nt, U=3.0, beta=0.125 * Nt, n_md=3, traj_length=0.3,
+                          cg_tol=1e-10, precision=hmc.PREC_MIXED, operand_mode=4, mu=mu, **kw)
+    b = hmc.Batch([p(*c) for c in chains])
+    phi = torch.zeros(b.total, dtype=torch.float64, device=DEV)
+    fields = [synth.gaussian_field(70 + i, Nt, 2 * L * L, 0.375, scale=0.5)
+              for i, (L, Nt, _) in enumerate(chains)]
+    for i, f in enumerate(fields):
+        b.view(phi, i).copy_(torch.from_numpy(f))
+    outs = b.trajectory(phi, 4, 0)
+    for i, (L, Nt, mu) in enumerate(chains):
+        single = hmc.Context(p(L, Nt, mu, team_ctas=1, inner_ctas=1))
+        sphi = torch.from_numpy(fields[i]).to(DEV)
+        o = single.trajectory(sphi, 4, 0, chain=i)
+        assert outs[i].status == 0 and o.status == 0
+        assert outs[i].dH == o.dH, (i, outs[i].dH, o.dH)
+        assert torch.equal(b.view(phi, i), sphi)

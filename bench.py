@@ -580,10 +580,21 @@ def run_batch(args):
         # otherwise finish last
         tuned = autotune.batch_shapes(plist, csize=args.batch_team)
         for p in tuned:
-            shapes["L%d_Nt%d" % (p.L, p.Nt)] = {"tile_slices": p.tile_slices,
-                                                "operand_mode": p.operand_mode,
-                                                "team_ctas": max(1, p.team_ctas),
-                                                "ru_delta": p.ru_delta}
+            # per class: the shape of its one-CTA chains (or, if all of them
+            # are teams, the team shape) and how many of its chains are teams
+            key = "L%d_Nt%d" % (p.L, p.Nt)
+            ent = shapes.setdefault(key, {"chains": 0, "team_chains": 0})
+            ent["chains"] += 1
+            if p.team_ctas > 1:
+                ent["team_chains"] += 1
+                ent.setdefault("team", {"team_ctas": p.team_ctas,
+                                        "tile_slices": p.tile_slices,
+                                        "operand_mode": p.operand_mode,
+                                        "ru_delta": p.ru_delta})
+            else:
+                ent.setdefault("one_cta", {"tile_slices": p.tile_slices,
+                                           "operand_mode": p.operand_mode,
+                                           "ru_delta": p.ru_delta})
         loop_params = [autotune.tune_ru(autotune.tune(p)) for p in plist[:args.loop_chains]]
         plist = tuned
     else:

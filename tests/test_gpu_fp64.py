@@ -163,6 +163,34 @@ def test_trajectory_fp64_matches_oracle_l3_nt8():
         phi_np = want["phi"]
 
 
+def test_l3_nt8_run_of_200_trajectories_matches_oracle():
+    """The full l3_nt8 run (200 FP64 trajectories from the prescribed
+    N(0, delta U) start): every trajectory starts from the oracle chain's
+    field and must reproduce its u, accept decision, Delta H and proposed
+    field to 1e-10.  (Two oracle runs at CG tolerances 1e-12 and 1e-14 agree
+    to 2e-13 on this chain, and |log u + Delta H| stays above 2e-3, so the
+    decisions are not on a knife's edge.)"""
+    w = synth.WORKLOADS["l3_nt8"]
+    c = hmc.Context(hmc.Params(L=w["L"], Nt=w["Nt"], kappa=w["kappa"], U=w["U"],
+                               beta=w["beta"], n_md=w["n_md"], traj_length=w["traj_length"],
+                               cg_tol=w["cg_tol"], precision=hmc.PREC_FP64))
+    phi_np = synth.start_field("l3_nt8")
+    phi = t64(phi_np)
+    accepted = 0
+    for traj in range(200):
+        phi.copy_(torch.from_numpy(phi_np))
+        want = run_oracle_traj(w, phi_np, traj)
+        out = c.trajectory(phi, w["seed"], traj)
+        assert out.u == want["u"], traj
+        assert bool(out.accept) == want["accept"], traj
+        assert abs(out.dH - want["dH"]) < 1e-10 * max(1.0, abs(want["H0"])), traj
+        assert out.max_true_residual < 1e-11
+        assert rel(phi.cpu().numpy(), want["phi"]) < 1e-10, traj
+        accepted += want["accept"]
+        phi_np = want["phi"]
+    assert accepted > 150
+
+
 def test_trajectory_deterministic_and_rejection_restores():
     w = synth.WORKLOADS["l3_nt8"]
     c = hmc.Context(hmc.Params(L=3, Nt=8, U=2.0, beta=2.0, n_md=2, traj_length=3.0,

@@ -126,9 +126,11 @@ typedef struct hmc_params {
                             much smaller energy violation at equal step) */
     double mu;           /* chemical potential (the sign-problem setting of
                             the paper's section on tensor networks, where
-                            p ~ det(M[phi,mu] M[phi,-mu]^dag)): taken into
-                            the hopping exponent, E = exp(delta (kappa h +
-                            mu)) = e^{delta mu} exp(delta kappa h), in every
+                            p ~ det(M[phi,mu] M[phi,-mu]^dag)), the mu of
+                            the particle-hole Hamiltonian's term
+                            + mu sum_x rho_x: M[phi,mu] is the particles'
+                            matrix, E = exp(delta (kappa h - mu)) =
+                            e^{-delta mu} exp(delta kappa h), in every
                             operator of the context (not in the Eq. (2.2)
                             operator of hmc_apply_brs); 0 = half filling */
 } hmc_params;

@@ -30,13 +30,16 @@ from . import lattice
 # transfer matrix
 # ---------------------------------------------------------------------------
 def transfer_matrix(h, delta_kappa, delta_mu=0.0):
-    """E = exp(delta*kappa*h + delta*mu) through the eigendecomposition of
-    the real symmetric h: E = Q diag(exp(delta*kappa*w + delta*mu)) Q^T.
-    The chemical potential mu (the sign-problem setting of the paper's
-    tensor-network section, p ~ det(M[phi,mu] M[phi,-mu]^dag)) enters the
-    hopping exponent; delta_mu = 0 is half filling."""
+    """E = exp(delta*kappa*h - delta*mu) through the eigendecomposition of
+    the real symmetric h: E = Q diag(exp(delta*kappa*w - delta*mu)) Q^T.
+    The chemical potential mu (the sign-problem setting of §5,
+    p ~ det(M[phi,mu] M[phi,-mu]^dag)) is the one of the particle-hole
+    Hamiltonian of §1, whose term + mu sum_x rho_x with
+    rho_x = p^dag p - h^dag h gives the particles the Boltzmann factor
+    e^{-delta mu} per slice (M[phi,mu]) and the holes e^{+delta mu}
+    (M[phi,-mu]); delta_mu = 0 is half filling."""
     w, Q = np.linalg.eigh(h)
-    return (Q * np.exp(delta_kappa * w + delta_mu)) @ Q.T
+    return (Q * np.exp(delta_kappa * w - delta_mu)) @ Q.T
 
 
 def time_signs(Nt):

@@ -198,8 +198,10 @@ int hmc_ctx_create(const hmc_params* p, hmc_ctx** out) {
     std::vector<double> E;
     build_transfer_matrix(p->L, v.delta * p->kappa, E);
     if (p->mu != 0.0) {
-        // chemical potential in the hopping exponent: exp(delta (kappa h + mu))
-        const double f = std::exp(v.delta * p->mu);
+        // chemical potential of the particles: H of §1 carries + mu sum_x rho_x,
+        // rho_x = p^dag p - h^dag h, so the particle transfer matrix is
+        // exp(delta (kappa h - mu)) = e^{-delta mu} exp(delta kappa h)
+        const double f = std::exp(-v.delta * p->mu);
         for (double& e : E) e *= f;
     }
     bool ok = true;

@@ -1,6 +1,6 @@
 """Chemical potential mu (the sign-problem setting of the paper's
 tensor-network section, p ~ det(M[phi,mu] M[phi,-mu]^dag)): the context's
-operator takes mu into the hopping exponent, E = exp(delta (kappa h + mu)).
+operator is the particles' one, E = exp(delta (kappa h - mu)).
 Parity against the FP64 oracle at the tolerances of the mu = 0 tests: FP64
 operator 1e-13, mixed operator 2e-6 (both tensor-core tile kinds), CG true
 residual 1e-10, mixed trajectory Delta H 1e-7."""

@@ -11,13 +11,14 @@ def test_free_correlator_closed_form(L, Nt, beta, kappa, mu):
     """phi = 0: M^{-1}'s (t, 0) block is E^t (1 + E^Nt)^{-1}; the k = 0 states
     of the two sublattices mix through h with energies +-3 kappa (each site
     has three neighbours), so C(t) = 1/2 sum_{e = +-3 kappa}
-    e^{t delta (e + mu)} / (1 + e^{beta (e + mu)}): Fermi factors."""
+    e^{t delta (e - mu)} / (1 + e^{beta (e - mu)}): Fermi factors of the
+    particles (energies -e + mu)."""
     delta = beta / Nt
     V = 2 * L * L
     E = ops.transfer_matrix(lattice.hopping_matrix(L), delta * kappa, delta * mu)
     got = obs.correlator_k0(E, np.zeros((Nt, V)))
     t = np.arange(Nt)
-    want = 0.5 * sum(np.exp(t * delta * (e + mu)) / (1.0 + np.exp(beta * (e + mu)))
+    want = 0.5 * sum(np.exp(t * delta * (e - mu)) / (1.0 + np.exp(beta * (e - mu)))
                      for e in (3.0 * kappa, -3.0 * kappa))
     assert np.allclose(got, want, rtol=1e-12, atol=1e-14)
 

@@ -178,35 +178,59 @@ def test_brs_adjoint_identity_large():
 
 
 # chemical potential (sign-problem setting, p ~ det(M[phi,mu] M[phi,-mu]^dag)):
-# mu enters the hopping exponent, E = exp(delta (kappa h + mu))
+# the §1 Hamiltonian's + mu sum_x rho_x gives the particles' transfer matrix
+# E = exp(delta (kappa h - mu))
 
 @pytest.mark.parametrize("L,Nt,beta,kappa,mu", [(1, 4, 1.0, 1.0, 0.3), (2, 6, 2.0, 1.0, -0.5),
                                                 (3, 8, 2.0, 1.0, 0.7), (3, 5, 3.0, -0.7, 1.1)])
 def test_free_determinant_with_mu_closed_form(L, Nt, beta, kappa, mu):
     """phi = 0: det M[0, mu] = prod over eigenvalues lam of h of
-    (1 + e^{beta (kappa lam + mu)}) -- the free grand-canonical partition
-    function of one species."""
+    (1 + e^{beta (kappa lam - mu)}) -- the free partition function of the
+    particles, single-particle energies -kappa lam + mu."""
     delta = beta / Nt
     E = ops.transfer_matrix(lattice.hopping_matrix(L), delta * kappa, delta * mu)
     sign, logdet = np.linalg.slogdet(ops.dense_M(E, np.zeros((Nt, 2 * L * L))))
     f = bloch_moduli(L)
     lam = np.concatenate([f, -f])
-    want = np.sum(np.log1p(np.exp(beta * (kappa * lam + mu))))
+    want = np.sum(np.log1p(np.exp(beta * (kappa * lam - mu))))
     assert abs(logdet - want) < 1e-11
     assert abs(sign - 1.0) < 1e-12
 
 
 @pytest.mark.parametrize("L,Nt,mu", [(1, 4, 0.4), (2, 3, -0.9)])
 def test_kappa_zero_with_mu_closed_form(L, Nt, mu):
-    """kappa = 0: det M = prod_x (1 + e^{beta mu} e^{i sum_t phi_{x,t}})."""
+    """kappa = 0: det M = prod_x (1 + e^{-beta mu} e^{i sum_t phi_{x,t}}): the
+    one-site trace over the particle's occupations n = 0, 1 of
+    e^{-beta mu n} e^{i Phi n} (energy + mu per particle, §1)."""
     rng = np.random.default_rng(16)
     V = 2 * L * L
     beta = 1.5
     E = ops.transfer_matrix(lattice.hopping_matrix(L), 0.0, beta / Nt * mu)
     phi = random_field(rng, Nt, V, 1.0)
-    want = np.prod(1.0 + np.exp(beta * mu) * np.exp(1j * phi.sum(axis=0)))
+    want = np.prod(1.0 + np.exp(-beta * mu) * np.exp(1j * phi.sum(axis=0)))
     got = np.linalg.det(ops.dense_M(E, phi))
     assert abs(got - want) <= 1e-12 * abs(want)
+
+
+@pytest.mark.parametrize("L,Nt,beta,kappa,mu", [(2, 4, 1.0, 1.0, 0.8), (3, 6, 2.0, 0.7, -0.4)])
+def test_particle_hole_identity_with_mu(L, Nt, beta, kappa, mu):
+    """det M[phi,-mu] = e^{i sum phi} e^{beta mu V} conj(det M[phi,mu]).
+    With B the product of the Nt slices' E D_t, det M[phi,mu] =
+    det(1 + e^{-beta mu} B); pulling B out of det(1 + e^{beta mu} B) leaves
+    det B e^{beta mu V} det(1 + e^{-beta mu} B^{-1}), det B = e^{i sum phi}
+    (tr h = 0), and B^{-1} is conj(B) transposed and conjugated by the
+    sublattice signs (h bipartite: P h P = -h).  Hence
+    |p[phi]| = e^{beta mu V} |det M[phi,mu]|^2: an HMC on |det M[phi,mu]|^2
+    samples the reweighting ensemble of §5."""
+    rng = np.random.default_rng(19)
+    V = 2 * L * L
+    delta = beta / Nt
+    h = lattice.hopping_matrix(L)
+    phi = random_field(rng, Nt, V, 1.0)
+    dp = np.linalg.det(ops.dense_M(ops.transfer_matrix(h, delta * kappa, delta * mu), phi))
+    dm = np.linalg.det(ops.dense_M(ops.transfer_matrix(h, delta * kappa, -delta * mu), phi))
+    want = np.exp(1j * phi.sum()) * np.exp(beta * mu * V) * np.conj(dp)
+    assert abs(dm - want) <= 1e-12 * abs(dm)
 
 
 def test_sign_problem_weight():

@@ -216,7 +216,7 @@ int hmc_trajectory(hmc_ctx* ctx, double* phi, uint64_t seed, uint64_t traj_index
 
 /* ---- Observables (M^{-1} sources) ---------------------------------------
  * Zero-momentum single-particle correlator on sublattice A, the correlator
- * whose decay in Euclidean time gives the single-particle gap (§4): source
+ * whose decay in Euclidean time gives the single-particle gap (§2): source
  * b = V_A^{-1/2} on the A sites (x < V/2) of slice 0; g = M^{-1} b =
  * M^dag (M M^dag)^{-1} b (CG to tol in `precision`, then the FP64 M^dag);
  * C[t] = V_A^{-1/2} sum_{x < V/2} g_t(x), t = 0..Nt-1.  phi: device double

@@ -1,6 +1,6 @@
 """Observables from M^{-1} sources (oracle; test infrastructure only).
 
-The paper (§4) measures the single-particle gap Delta from the decay of a
+The paper (§2) measures the single-particle gap Delta from the decay of a
 single-particle correlator; it names the observable, not its estimator.
 Reading taken: the zero-momentum correlator on sublattice A from one
 source b = V_A^{-1/2} on the A sites of slice 0,

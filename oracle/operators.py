@@ -32,7 +32,7 @@ from . import lattice
 def transfer_matrix(h, delta_kappa, delta_mu=0.0):
     """E = exp(delta*kappa*h - delta*mu) through the eigendecomposition of
     the real symmetric h: E = Q diag(exp(delta*kappa*w - delta*mu)) Q^T.
-    The chemical potential mu (the sign-problem setting of §5,
+    The chemical potential mu (the sign-problem setting of §3,
     p ~ det(M[phi,mu] M[phi,-mu]^dag)) is the one of the particle-hole
     Hamiltonian of §1, whose term + mu sum_x rho_x with
     rho_x = p^dag p - h^dag h gives the particles the Boltzmann factor

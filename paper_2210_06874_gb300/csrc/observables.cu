@@ -1,6 +1,6 @@
 // observables.cu -- the zero-momentum single-particle correlator on
 // sublattice A from one M^{-1} source (the correlator whose decay in
-// Euclidean time gives the single-particle gap Delta of the paper's §4).
+// Euclidean time gives the single-particle gap Delta of the paper's §2).
 //
 // Source b: V_A^{-1/2} on the A sites (indices 0..V/2-1, sublattice-major)
 // of slice 0, zero elsewhere.  g = M^{-1} b = M^dag (M M^dag)^{-1} b (CG in

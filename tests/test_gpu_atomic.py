@@ -3,7 +3,7 @@
 The FP64 chain follows the oracle's chain trajectory by trajectory over 610
 trajectories (same Philox draws, identical accept decisions, fields within
 1e-9).  Both precisions reproduce <cos Phi_x> of the atomic-limit weight
-N(0, beta U) x (2 + 2 cos Phi), the distribution pinned against the §2
+N(0, beta U) x (2 + 2 cos Phi), the distribution pinned against the §1
 Hamiltonian in test_oracle_atomic.py, within 4 standard errors.
 """
 import numpy as np

@@ -1,6 +1,6 @@
 """Atomic-limit pins of the oracle's weight and sampler (CPU only).
 
-At kappa = 0 the Hamiltonian of §2 in the particle-hole basis,
+At kappa = 0 the Hamiltonian of §1 in the particle-hole basis,
 H = (U/2) sum_x rho_x^2 + mu sum_x rho_x with rho_x = p^dag p - h^dag h,
 falls apart into independent sites with four states each: rho = 0 twice,
 rho = +1 and rho = -1, so every site contributes

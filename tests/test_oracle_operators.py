@@ -221,7 +221,7 @@ def test_particle_hole_identity_with_mu(L, Nt, beta, kappa, mu):
     (tr h = 0), and B^{-1} is conj(B) transposed and conjugated by the
     sublattice signs (h bipartite: P h P = -h).  Hence
     |p[phi]| = e^{beta mu V} |det M[phi,mu]|^2: an HMC on |det M[phi,mu]|^2
-    samples the reweighting ensemble of §5."""
+    samples the reweighting ensemble of §3."""
     rng = np.random.default_rng(19)
     V = 2 * L * L
     delta = beta / Nt

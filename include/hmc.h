@@ -4,8 +4,9 @@
  *
  * The operator.  Lattice: L x L unit cells of the honeycomb lattice, two
  * sites each, V = 2 L^2 sites, periodic (§1, Fig. 1; §4).  With delta =
- * beta / Nt, h the nearest-neighbour adjacency and E = exp(delta*kappa*h),
- * the fermion matrix on space-time vectors psi[t][x] is
+ * beta / Nt, h the nearest-neighbour adjacency and E = exp(delta*kappa*h)
+ * (E = exp(delta*(kappa*h - mu)) at a chemical potential mu, see
+ * hmc_params), the fermion matrix on space-time vectors psi[t][x] is
  *
  *     (M psi)_t     = psi_t - s_t     * E diag(exp(i phi_{t-1})) psi_{t-1}
  *     (M^dag psi)_t = psi_t - s_{t+1} * diag(exp(-i phi_t)) E psi_{t+1}
@@ -156,7 +157,7 @@ typedef struct hmc_traj_out {
 
 typedef struct hmc_ctx hmc_ctx;
 
-/* Build h and E = exp(delta*kappa*h) (FP64, plus its FP16 hi/lo split for
+/* Build h and E = exp(delta*(kappa*h - mu)) (FP64, plus its FP16 hi/lo split for
  * the MIXED path) for the lattice in *p and allocate workspaces on the
  * current CUDA device.  *out receives the context.
  * Errors: HMC_ERR_BAD_ARG (L < 1, Nt < 1, U <= 0, ...), HMC_ERR_CUDA. */
@@ -206,8 +207,9 @@ int hmc_action(hmc_ctx* ctx, const double* phi, const void* chi, const void* x, 
 
 /* One HMC trajectory (§2) on device field phi (in/out, double [Nt][V]):
  * momenta pi ~ exp(-pi^2/2) and noise rho ~ exp(-rho^dag rho) from Philox
- * streams (seed, traj_index, chain), chi = M rho, leapfrog of n_md steps
- * (drift phi += eps*delta*pi, kick pi -= eps*delta*dS/dphi), Metropolis
+ * streams (seed, traj_index, chain), chi = M rho, n_md molecular-dynamics
+ * steps of params.integrator (leapfrog or the minimum-norm integrator; drift
+ * phi += c*eps*delta*pi, kick pi -= c*eps*delta*dS/dphi), Metropolis
  * with u from the generator.  On rejection phi is restored.  The whole
  * trajectory runs in one persistent launch; *out (host) is filled and the
  * stream synchronised.  Precision: params.precision. */

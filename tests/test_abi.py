@@ -54,12 +54,35 @@ def bad(**kw):
                                          ("L", 30000), ("operand_mode", 5),
                                          ("cluster_mode", 3), ("cluster_mode", -1),
                                          ("integrator", 2), ("integrator", -1),
-                                         ("mu", float("nan")), ("mu", 100.0)])
+                                         ("mu", float("nan")), ("mu", 100.0),
+                                         ("traj_length", 0.0), ("kappa", float("inf")),
+                                         ("team_ctas", -1), ("inner_ctas", 2000),
+                                         ("tile_slices", 12), ("tile_slices", 64)])
 def test_ctx_create_rejects_bad_params(lib, field, value):
     h = ctypes.c_void_p()
     p = bad(**{field: value})
     assert lib.hmc_ctx_create(ctypes.byref(p), ctypes.byref(h)) == hmc.HMC_ERR_BAD_ARG
     assert not h.value
+
+
+@pytest.mark.parametrize("kw,ok", [(dict(operand_mode=4, tile_slices=64), True),
+                                   (dict(operand_mode=4, tile_slices=65), False),
+                                   (dict(operand_mode=1, tile_slices=32), True),
+                                   (dict(mu=4.9 * 8 / 2.0), True),      # |delta mu| = 4.9
+                                   (dict(mu=5.1 * 8 / 2.0), False)])
+def test_ctx_create_limits(lib, kw, ok):
+    """Parameters at the edge of what the kernels take pass the host checks
+    (then the context is created, or the missing device is reported);
+    just beyond the edge they are refused before any CUDA call."""
+    h = ctypes.c_void_p()
+    p = bad(**kw)
+    code = lib.hmc_ctx_create(ctypes.byref(p), ctypes.byref(h))
+    if ok:
+        assert code in (hmc.HMC_OK, hmc.HMC_ERR_CUDA)
+        if code == hmc.HMC_OK:
+            lib.hmc_ctx_destroy(h)
+    else:
+        assert code == hmc.HMC_ERR_BAD_ARG and not h.value
 
 
 def test_null_arguments_rejected(lib):

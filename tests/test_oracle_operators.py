@@ -142,6 +142,42 @@ def test_brs_free_closed_form(L, Nt, beta):
     assert abs(logdet - want) < 1e-11
 
 
+def brs_kappa_zero_det(L, phi):
+    """det of Eq. (2.2) at kappa = 0: every site is a cyclic bidiagonal
+    Nt x Nt block.  A site: -diag(e^{i phi_t}) plus the forward shift with
+    the wrap -1, det = (-1)^Nt (1 + e^{i Phi}); B site: 1 minus the
+    backward shift weighted by e^{-i phi_t} with the wrap -1,
+    det = 1 + e^{-i Phi}; Phi = sum_t phi_t.  Sites x < L^2 are A."""
+    Nt, V = phi.shape
+    Phi = phi.sum(axis=0)
+    a = (-1.0) ** Nt * (1.0 + np.exp(1j * Phi[:V // 2]))
+    b = 1.0 + np.exp(-1j * Phi[V // 2:])
+    return np.prod(a) * np.prod(b)
+
+
+@pytest.mark.parametrize("L,Nt", [(1, 3), (2, 4), (2, 5)])
+def test_brs_kappa_zero_closed_form(L, Nt):
+    rng = np.random.default_rng(23)
+    V = 2 * L * L
+    phi = random_field(rng, Nt, V, 1.0)
+    got = np.linalg.det(ops.dense_M_brs(L, phi, 0.25, 0.0))
+    want = brs_kappa_zero_det(L, phi)
+    assert abs(got - want) <= 1e-12 * abs(want)
+
+
+def test_planted_brs_sublattice_swap_is_caught(monkeypatch):
+    """The phases of Eq. (2.2) on the wrong sublattices (A backward with
+    e^{-i phi}, B forward with e^{+i phi}) change the complex determinant."""
+    L, Nt = 2, 4
+    rng = np.random.default_rng(23)
+    V = 2 * L * L
+    phi = random_field(rng, Nt, V, 1.0)
+    real = lattice.sublattice
+    monkeypatch.setattr(lattice, "sublattice", lambda L_: 1 - real(L_))
+    got = np.linalg.det(ops.dense_M_brs(L, phi, 0.25, 0.0))
+    assert abs(got - brs_kappa_zero_det(L, phi)) > 1e-3 * abs(got)
+
+
 @pytest.mark.parametrize("L,Nt", [(1, 2), (2, 3), (3, 4)])
 def test_brs_dense_vs_matrix_free(L, Nt):
     rng = np.random.default_rng(3)

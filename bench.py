@@ -268,34 +268,115 @@ def cpu_oracle_rate_single_thread(name, prec, sample_s, phi_np=None, integrator=
         os.unlink(path)
 
 
+def cpu_oracle_apply_rate(name, sample_s):
+    """Time the oracle's matrix-free M (as it stands) on the workload's
+    lattice: applications per second over about sample_s seconds."""
+    import numpy as np
+    from oracle import lattice, operators as ops
+    from paper_2210_06874_gb300 import synth
+    w = synth.WORKLOADS[name]
+    L, Nt = w["L"], w["Nt"]
+    V, delta = 2 * L * L, w["beta"] / w["Nt"]
+    E = ops.transfer_matrix(lattice.hopping_matrix(L), delta * w["kappa"])
+    phi = synth.gaussian_field(w["seed"], Nt, V, delta * w["U"])
+    psi = synth.complex_gaussian(w["seed"] + 1, Nt, V)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        psi = ops.apply_M(E, phi, psi)
+        psi /= np.linalg.norm(psi)
+        n += 1
+        if time.perf_counter() - t0 > sample_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "M-applications/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": "%d oracle applications of M on %s, %.1f s; NumPy FP64, BLAS threads "
+                      "as configured" % (n, name, dt)}
+
+
+def cpu_oracle_batch_rate(n_chains, sample_s):
+    """Time the oracle on the batched workload's chains in batch order, one
+    trajectory each from a cold start, until about sample_s seconds of work
+    are done (at least one chain): chains done / time."""
+    import numpy as np
+    from oracle import hmc as ohmc, lattice, operators as ops
+    from paper_2210_06874_gb300 import synth
+    specs = synth.batch256(n_chains=n_chains)
+    t0 = time.perf_counter()
+    n = 0
+    for i, c in enumerate(specs):
+        V, delta = 2 * c["L"] ** 2, c["beta"] / c["Nt"]
+        E = ops.transfer_matrix(lattice.hopping_matrix(c["L"]), delta * c["kappa"])
+        ohmc.trajectory(E, np.zeros((c["Nt"], V)), delta, c["U"],
+                        c["traj_length"] / c["n_md"], c["n_md"], synth.BASE_SEED + 3, 0, i,
+                        tol=c["cg_tol"], max_iter=200000)
+        n += 1
+        if time.perf_counter() - t0 > sample_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "trajectories/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": "oracle trajectories of the first %d of the %d chains (batch order, cold "
+                      "start), %.1f s; NumPy FP64, BLAS threads as configured"
+                      % (n, n_chains, dt)}
+
+
 # ----------------------------------------------------------------- reference arm
 def run_reference(args):
+    """The oracle as it stands, on the host cores, for the workload and
+    metric of our arm: trajectories/s (single chain or the batched chains)
+    or M-applications/s (--mode apply)."""
     rank, _, world = dist_env()
     if rank != 0:
         return
     from paper_2210_06874_gb300 import synth
     name = args.workload
-    w = synth.WORKLOADS[name]
-    prec = args.precision or w["precision"]
-    rates = []
+    sample_s = min(args.cpu_sample_s, 20.0)
+    if args.mode == "brs":
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "the oracle's Eq. (2.2) operator holds the dense V x V hopping "
+                          "matrix: 3.5 GB and 2e11 flops per application at L = 102"}),
+              flush=True)
+        return
+    batch = name.startswith("batch")
+    apply = args.mode == "apply" and not batch
+    rates, samples, secs = [], [], []
     for k in range(args.warmup + args.steps):
-        r = cpu_oracle_rate(name, prec, min(args.cpu_sample_s, 20.0),
-                            integrator=args.integrator, n_md=args.n_md)
+        t0 = time.perf_counter()
+        if batch:
+            r = cpu_oracle_batch_rate(args.chains, sample_s)
+        elif apply:
+            r = cpu_oracle_apply_rate(name, sample_s)
+        else:
+            r = cpu_oracle_rate(name, None, sample_s, integrator=args.integrator,
+                                n_md=args.n_md)
         if k >= args.warmup:
             rates.append(r["value"])
+            samples.append(r["sample"])
+            secs.append(time.perf_counter() - t0)
     value = statistics.mean(rates)
+    unit = "M-applications/s" if apply else "trajectories/s"
+    if batch:
+        config = {"workload": name, "precision": "fp64 (oracle)", "chains": args.chains}
+    else:
+        w = synth.WORKLOADS[name]
+        config = {"workload": name, "precision": "fp64 (oracle)", "L": w["L"], "Nt": w["Nt"]}
+        if apply:
+            config["mode"] = "apply"
+        else:
+            config.update(n_md=args.n_md or w["n_md"], integrator=args.integrator)
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "trajectories/s",
+        "impl": "reference", "metric": METRIC, "value": value, "unit": unit,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": name, "precision": "fp64 (oracle)", "L": w["L"], "Nt": w["Nt"],
-                   "n_md": args.n_md or w["n_md"], "integrator": args.integrator},
-        "cpu_baseline": {"value": value, "unit": "trajectories/s", "cores": os.cpu_count(),
+        "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+        "cpu_baseline": {"value": value, "unit": unit, "cores": os.cpu_count(),
                          "kind": "oracle",
-                         "sample": "each step: oracle trajectories of %s for ~%.0f s"
-                                   % (name, min(args.cpu_sample_s, 20.0))},
-        "e2e": {"value": value, "unit": "trajectories/s", "h2d_bytes_per_step": 0,
+                         "sample": "each step ~%.0f s of oracle work; last step: %s"
+                                   % (sample_s, samples[-1])},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

@@ -45,3 +45,16 @@ def test_reference_arm_under_torchrun_two_ranks():
     lines = json_lines(r.stdout)
     assert len(lines) == 1                      # rank 0 only
     check_line(lines[0], 2)
+
+
+def test_reference_arm_apply_mode():
+    """--mode apply: the oracle's M-applications/s on the workload's lattice."""
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--mode", "apply",
+                        "--workload", "l3_nt8", "--steps", "1", "--warmup", "0",
+                        "--cpu-sample-s", "0.2"], cwd=ROOT, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    (line,) = json_lines(r.stdout)
+    assert line["impl"] == "reference" and line["unit"] == "M-applications/s"
+    assert line["value"] > 0 and line["config"]["mode"] == "apply"
+    assert line["cpu_baseline"]["unit"] == "M-applications/s"

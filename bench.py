@@ -634,6 +634,8 @@ def run_apply(args):
             "per_call_from_python_us": eager_ms * 1e3,
             "gpu_launches": n * 2 if prec != "fp64" else n * 2,
             "roofline": roof, "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_apply_rate(name, args.cpu_sample_s)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -813,6 +815,8 @@ def run_batch(args):
                      "peak_source": "%s bf16 dense sustained (fp16 has the same rate)" % kind},
         "clocks": clk,
     }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_batch_rate(args.chains, args.cpu_sample_s)
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -134,6 +134,12 @@ typedef struct hmc_params {
                             e^{-delta mu} exp(delta kappa h), in every
                             operator of the context (not in the Eq. (2.2)
                             operator of hmc_apply_brs); 0 = half filling */
+    int ru_every;        /* mixed CG: a reliable update at the latest after
+                            this many FP32 iterations (0 selects 1000), so a
+                            stalled FP32 recursion still reaches an FP64
+                            residual check; two checks in a row that do not
+                            halve the true residual switch the rest of the
+                            solve to FP64 CG iterations */
 } hmc_params;
 
 typedef struct hmc_cg_stats {
@@ -141,6 +147,7 @@ typedef struct hmc_cg_stats {
     int reliable_updates;    /* FP64 residual recomputations (MIXED) */
     double true_residual;    /* |chi - M M^dag x| / |chi| in FP64 */
     int status;              /* hmc_status of the solve */
+    int fp64_iterations;     /* MIXED: FP64 CG iterations after a stall (0 normally) */
 } hmc_cg_stats;
 
 typedef struct hmc_traj_out {
@@ -153,6 +160,7 @@ typedef struct hmc_traj_out {
     int reliable_updates;
     double max_true_residual;
     int status;
+    int fp64_iterations;     /* MIXED: FP64 CG iterations of stalled solves */
 } hmc_traj_out;
 
 typedef struct hmc_ctx hmc_ctx;
@@ -289,13 +297,13 @@ int hmc_rng_draw(uint64_t seed, uint32_t stream_id, uint64_t traj, uint32_t chai
 /* FP64 CG solve of (M M^dag) x = chi that allocates no device memory.
  *
  * The paper has no counterpart; this is a library convenience.  Callers that
- * may not call cudaMalloc -- code running under CUDA graph capture, hosts
- * whose device memory comes from a framework pool or a fixed real-time
- * budget, plugins barred from growing the device heap -- cannot create an
- * hmc_ctx.  This call needs none: it runs the same FP64 CG as hmc_cg_solve
- * with HMC_PREC_FP64 (same algorithm, stopping rule and stats), with its
- * scratch in one static device array of about 2.1 MB that every GPU which
- * loads the library holds until the process exits.
+ * may not call cudaMalloc -- hosts whose device memory comes from a
+ * framework pool or a fixed real-time budget, plugins barred from growing
+ * the device heap -- cannot create an hmc_ctx.  This call needs none: it
+ * runs the same FP64 CG as hmc_cg_solve with HMC_PREC_FP64 (same algorithm,
+ * stopping rule and stats), with its scratch in one static device array of
+ * about 2.1 MB that every GPU which loads the library holds until the
+ * process exits.
  *
  *   E      device, double [V][V], the transfer matrix exp(delta*kappa*h),
  *          row-major and exactly symmetric (e.g. from hmc_get_transfer_matrix)
@@ -304,14 +312,39 @@ int hmc_rng_draw(uint64_t seed, uint32_t stream_id, uint64_t traj, uint32_t chai
  *   phi    device, double [Nt][V]; chi, x device complex128 [Nt][V]
  *   stats  host; the call synchronises `stream`
  *
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call on a device shares the one array:
- * calls that overlap on the GPU (other streams, other host threads) race
- * and give wrong results; serialise them.  The barrier, status and output
- * words are cleared on every call.  Errors as hmc_cg_solve. */
+ * The call copies its statistics to the host and synchronises the stream,
+ * so it cannot be recorded into a CUDA graph: on a stream that is being
+ * captured it returns HMC_ERR_UNSUPPORTED before enqueuing anything, and the
+ * capture stays valid.  The first call on each device (and the first after
+ * that device's context was replaced, e.g. by cudaDeviceReset) looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current.
+ * Every call on a device shares the one array: calls that overlap on the
+ * GPU (other streams, other host threads) race and give wrong results;
+ * serialise them.  The barrier, status and output words are cleared on
+ * every call.  Errors as hmc_cg_solve. */
 int hmc_cg_solve_noalloc(const double* E, int L, int Nt, const double* phi, const void* chi,
                          void* x, double tol, int max_iter, hmc_cg_stats* stats, void* stream);
+
+/* ---- Bounded waits ---------------------------------------------------------
+ * Every spin of the library's kernels (team barriers, mbarrier waits of the
+ * tensor-core pipelines, cluster exchanges) gives up after a time limit and
+ * records HMC_ERR_TIMEOUT, which the next synchronising call returns; the
+ * kernel then leaves its waits and frees what it holds, so the context stays
+ * usable.  The paper has no counterpart (failure handling of this library).
+ *
+ * hmc_ctx_set_wait_limit: the limit of every wait of kernels launched on
+ * this context from now on, in seconds (0 restores the default of 20 s; at
+ * most 3600).  A limit shorter than a whole solve makes the CTAs that wait
+ * out the FP32 iterations time out: keep the default in normal use.
+ * Synchronises the device.
+ *
+ * hmc_debug_team_padding: host-side fault injection for testing the timeout
+ * path.  Every team barrier of this context's later persistent launches
+ * expects extra_ctas (0..1024) CTAs more than were launched, so the first
+ * one never completes and its bounded wait runs out.  0 restores normal
+ * operation. */
+int hmc_ctx_set_wait_limit(hmc_ctx* ctx, double seconds);
+int hmc_debug_team_padding(hmc_ctx* ctx, int extra_ctas);
 
 /* Library version string (static storage). */
 const char* hmc_version(void);

@@ -143,6 +143,7 @@ static int valid_params(const hmc_params* p) {
     if (p->operand_mode < 0 || p->operand_mode > 4) return 0;
     if (p->cluster_mode < 0 || p->cluster_mode > 2) return 0;
     if (p->integrator < 0 || p->integrator > 1) return 0;
+    if (p->ru_every < 0) return 0;
     // |delta mu| <= 5: the scaled E keeps its FP16 split in range
     if (!std::isfinite(p->mu) || std::fabs(p->mu * p->beta / p->Nt) > 5.0) return 0;
     if (p->operand_mode == 4) {
@@ -218,7 +219,7 @@ int hmc_ctx_create(const hmc_params* p, hmc_ctx** out) {
     v.pi = (double*)ctx_alloc(c, N * sizeof(double), &ok);
     v.phi_old = (double*)ctx_alloc(c, N * sizeof(double), &ok);
     v.bar = (unsigned*)ctx_alloc(c, 8 * sizeof(unsigned), &ok);
-    v.status = (int*)ctx_alloc(c, sizeof(int), &ok);
+    v.status = (int*)ctx_alloc(c, kStatusBlockBytes, &ok);
     v.partials = (double*)ctx_alloc(c, sizeof(double) * kPartialDoubles, &ok);
     v.scalars = (double*)ctx_alloc(c, sizeof(double) * kNumScalars, &ok);
     if (ok && cudaMemcpy(dE, E.data(), E.size() * sizeof(double), cudaMemcpyHostToDevice) !=
@@ -312,6 +313,7 @@ int hmc_cg_solve(hmc_ctx* c, const double* phi, const void* chi, void* x, double
     stats->true_residual = c->scalars_host[1];
     stats->status = (int)c->scalars_host[2];
     stats->reliable_updates = (int)c->scalars_host[3];
+    stats->fp64_iterations = (int)c->scalars_host[4];
     return stats->status;
 }
 
@@ -378,8 +380,24 @@ int hmc_trajectory(hmc_ctx* c, double* phi, uint64_t seed, uint64_t traj_index, 
     out->cg_solves = (int)v[kTrajSolves];
     out->reliable_updates = (int)v[kTrajRU];
     out->max_true_residual = v[kTrajMaxRes];
+    out->fp64_iterations = (int)v[kTrajFp64Iters];
     out->status = dev != 0 ? dev : (int)v[kTrajStatus];
     return out->status;
+}
+
+int hmc_ctx_set_wait_limit(hmc_ctx* c, double seconds) {
+    if (!c || !(seconds >= 0.0) || seconds > 3600.0) return HMC_ERR_BAD_ARG;
+    const uint64_t ns = (uint64_t)(seconds * 1e9);
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(c->view.status + 2, &ns, sizeof(ns), cudaMemcpyHostToDevice) != cudaSuccess)
+        return HMC_ERR_CUDA;
+    return HMC_OK;
+}
+
+int hmc_debug_team_padding(hmc_ctx* c, int extra_ctas) {
+    if (!c || extra_ctas < 0 || extra_ctas > kMaxTeam) return HMC_ERR_BAD_ARG;
+    c->view.team_pad = extra_ctas;
+    return HMC_OK;
 }
 
 int hmc_rng_draw(uint64_t seed, uint32_t stream_id, uint64_t traj, uint32_t chain, int64_t n,

@@ -75,9 +75,16 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Every spin in this library gives up after this long and records
-// HMC_ERR_TIMEOUT instead of waiting forever.
+// Every spin in this library gives up after a time limit and records
+// HMC_ERR_TIMEOUT instead of waiting forever.  The limit lives in the
+// status block next to the status word: int status, int (unused), uint64
+// limit in ns at byte offset 8; zero there selects the default below.
 constexpr uint64_t kWaitLimitNs = 20ull * 1000ull * 1000ull * 1000ull;  // 20 s
+constexpr size_t kStatusBlockBytes = 16;
+__device__ __forceinline__ uint64_t wait_limit_ns(const int* status) {
+    const uint64_t v = *reinterpret_cast<const volatile uint64_t*>(status + 2);
+    return v ? v : kWaitLimitNs;
+}
 
 // ---------------------------------------------------------------- team
 // A team is a set of co-resident CTAs of one persistent (cooperative)
@@ -254,7 +261,7 @@ __device__ inline bool cluster_wait(const Team& tm) {
         if ((n & 1023u) == 0) {
             if (t0 == 0) t0 = global_ns();
             if (team_failed(tm)) return false;
-            if (global_ns() - t0 > kWaitLimitNs) {
+            if (global_ns() - t0 > wait_limit_ns(tm.status)) {
                 set_status(tm.status, HMC_ERR_TIMEOUT);
                 return false;
             }
@@ -389,7 +396,7 @@ __device__ inline bool team_sync(Team& tm, double* v) {
         for (unsigned n = 1; ld_acquire_u32(&tm.bar[1]) == g; ++n) {
             if ((n & 1023u) == 0) {
                 if (team_failed(tm)) { ok = 0; break; }
-                if (global_ns() - t0 > kWaitLimitNs) {
+                if (global_ns() - t0 > wait_limit_ns(tm.status)) {
                     set_status(tm.status, HMC_ERR_TIMEOUT);
                     ok = 0;
                     break;

@@ -33,7 +33,10 @@ struct ChainView {
     float2 *cis_f, *r_f, *p_f, *p2_f, *q_f, *x_f;
     // team synchronisation
     unsigned* bar;              // 2 words
-    int* status;                // device status word
+    int* status;                // device status block (kStatusBlockBytes): status
+                                // word, then the wait limit (common.cuh)
+    int team_pad;               // testing only: CTAs every team barrier expects
+                                // beyond those launched (0 in normal use)
     double* partials;           // kSlots * kMaxTeam * kVals
     double* scalars;            // per-call scalar outputs (see kernels)
 };

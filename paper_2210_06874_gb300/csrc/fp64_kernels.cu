@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(NTHR) k_force(ChainView c, const double* phi,
 __device__ __forceinline__ Team make_team(const ChainView& c) {
     Team tm;
     tm.rank = blockIdx.x;
-    tm.size = gridDim.x;
+    tm.size = gridDim.x + c.team_pad;
     tm.bar = c.bar;
     tm.status = c.status;
     tm.partials = c.partials;

@@ -158,18 +158,23 @@ struct CgResult {
     int status;
 };
 
-// Conjugate gradient on M M^dag from x = 0 (FP64), CG vectors in the chain
-// workspace (r, p, q).  cis must hold exp(i phi).  Ends with the FP64 true
-// residual, which leaves chi - M M^dag x in r.
+// Conjugate gradient on M M^dag (FP64), CG vectors in the chain workspace
+// (r, p, q), from x = 0 or (warm) from the x given, whose residual
+// chi - M M^dag x then starts the iteration.  cis must hold exp(i phi).
+// Ends with the FP64 true residual, which leaves chi - M M^dag x in r and
+// M^dag x in q.
 __device__ inline bool cg_solve(const ChainView& c, Team& tm, const double2* chi, double2* x,
-                         double tol, int max_iter, CgResult& res, Smem& sm) {
+                         double tol, int max_iter, CgResult& res, Smem& sm,
+                         bool warm = false) {
     double2 *r = c.r, *p = c.p, *q = c.q;
     double v1[1] = {0.0};
     HMC_TEAM_ELEMS(e, c, tm) {
         const double2 ch = chi[e];
-        x[e] = make_double2(0.0, 0.0);
-        r[e] = ch;
-        p[e] = ch;
+        if (!warm) {
+            x[e] = make_double2(0.0, 0.0);
+            r[e] = ch;
+            p[e] = ch;
+        }
         v1[0] += ch.x * ch.x + ch.y * ch.y;
     }
     if (!team_sum<1>(tm, v1)) return false;
@@ -187,9 +192,21 @@ __device__ inline bool cg_solve(const ChainView& c, Team& tm, const double2* chi
     ea.x = x;
     ea.r = r;
     ea.p = p;
+    if (warm) {
+        // r = chi - M (M^dag x), p = r
+        apply_team<true, EPI_STORE>(c, tm, x, q, ea, sm);
+        if (!team_barrier(tm)) return false;
+        ea.chi = chi;
+        double vr[1] = {apply_team<false, EPI_RESIDUAL>(c, tm, q, nullptr, ea, sm)};
+        if (!team_sum<1>(tm, vr)) return false;
+        rr = vr[0];
+        HMC_TEAM_ELEMS(e, c, tm) p[e] = r[e];
+        if (!team_barrier(tm)) return false;
+        if (!finite_d(rr)) res.status = HMC_ERR_NONFINITE;
+    }
     int it = 0;
-    bool conv = false;
-    while (it < max_iter) {
+    bool conv = res.status == HMC_OK && rr <= stop;
+    while (!conv && res.status == HMC_OK && it < max_iter) {
         double vq[1] = {apply_team<true, EPI_STORE>(c, tm, p, q, ea, sm)};  // q = M^dag p
         if (!team_sum<1>(tm, vq)) return false;
         const double qq = vq[0];

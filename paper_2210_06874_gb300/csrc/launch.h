@@ -47,7 +47,7 @@ __host__ __device__ inline double md_kick(const TrajArgs& a, int m) {
 // Slots of ChainView::scalars written by the trajectory kernels.
 enum TrajSlot : int {
     kTrajDH = 0, kTrajH0, kTrajH1, kTrajU, kTrajAccept, kTrajIters, kTrajSolves,
-    kTrajRU, kTrajMaxRes, kTrajStatus, kNumScalars = 16
+    kTrajRU, kTrajMaxRes, kTrajStatus, kTrajFp64Iters, kNumScalars = 16
 };
 
 int launch_cis_f64(const ChainView& c, const double* phi, cudaStream_t s);

@@ -1,16 +1,20 @@
 // noalloc.cu -- hmc_cg_solve_noalloc: the FP64 CG solve for callers that
 // cannot allocate device memory.
 //
-// Some callers may not call cudaMalloc at all: code that runs while a CUDA
-// graph is being captured (allocation is not a capturable operation), hosts
-// whose device memory is handed out by a framework's own pool or by a
-// fixed-budget real-time allocator, and plugins loaded into a process that
-// forbids its extensions from growing the device heap.  They cannot create
-// an hmc_ctx, whose workspaces are cudaMalloc'ed.  This entry point runs the
-// same persistent FP64 CG kernel as hmc_cg_solve(prec = HMC_PREC_FP64), but
-// its scratch (the exp(i phi) table, the CG vectors r, p, q, the team
-// partial sums, the barrier and status words) lives in one file-scope
-// __device__ array that every GPU loading the library holds until exit.
+// Some callers may not call cudaMalloc at all: hosts whose device memory is
+// handed out by a framework's own pool or by a fixed-budget real-time
+// allocator, and plugins loaded into a process that forbids its extensions
+// from growing the device heap.  They cannot create an hmc_ctx, whose
+// workspaces are cudaMalloc'ed.  This entry point runs the same persistent
+// FP64 CG kernel as hmc_cg_solve(prec = HMC_PREC_FP64), but its scratch (the
+// exp(i phi) table, the CG vectors r, p, q, the team partial sums, the
+// barrier and status words) lives in one file-scope __device__ array that
+// every GPU loading the library holds until exit.  The call waits for its
+// own result (it copies the statistics to the host and synchronises the
+// stream), so it refuses to run on a stream that is being captured into a
+// CUDA graph.
+#include <cuda.h>
+
 #include <cstring>
 #include <mutex>
 
@@ -39,28 +43,55 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
-void* g_scratch_addr[kMaxDevices];   // device address of the array, per device
-int g_num_sms[kMaxDevices];
+struct DeviceScratch {
+    CUcontext ctx;      // context the address was looked up in
+    void* addr;         // device address of the array in that context
+    int num_sms;
+};
+DeviceScratch g_scratch[kMaxDevices];
 
-// Once per device, with that device current: the host-side name of the
-// array is only a stand-in, so look up its device address.
+// The current context of the calling thread (driver entry point, so the
+// library needs no link against the driver library).
+CUcontext current_context() {
+    using Fn = CUresult (*)(CUcontext*);
+    static Fn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<Fn>(p);
+    });
+    CUcontext c = nullptr;
+    if (fn && fn(&c) != CUDA_SUCCESS) c = nullptr;
+    return c;
+}
+
+// Set-up once per device (and again if that device's context was replaced,
+// e.g. after cudaDeviceReset), with the device current: the host-side name
+// of the array is only a stand-in, so look up its device address.
 int scratch_for_current_device(void** addr, int* num_sms) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return HMC_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return HMC_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
+    DeviceScratch& d = g_scratch[dev];
+    const CUcontext ctx = current_context();
+    if (!d.addr || !ctx || d.ctx != ctx) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
             return HMC_ERR_CUDA;
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return HMC_ERR_CUDA;
-        g_num_sms[dev] = sms;
-        g_scratch_addr[dev] = p;
+        d.num_sms = sms;
+        d.addr = p;
+        d.ctx = current_context();
     }
-    *addr = g_scratch_addr[dev];
-    *num_sms = g_num_sms[dev];
+    *addr = d.addr;
+    *num_sms = d.num_sms;
     return HMC_OK;
 }
 
@@ -74,6 +105,16 @@ extern "C" int hmc_cg_solve_noalloc(const double* E, int L, int Nt, const double
     if (!E || !phi || !chi || !x || chi == x || !stats) return HMC_ERR_BAD_ARG;
     if (L < 1 || Nt < 1 || !(tol > 0.0) || max_iter < 1) return HMC_ERR_BAD_ARG;
     std::memset(stats, 0, sizeof(*stats));
+    cudaStream_t s = (cudaStream_t)stream;
+    // a stream under graph capture: refuse before anything is enqueued (the
+    // call synchronises and reads its result on the host), so the caller's
+    // capture stays valid
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return HMC_ERR_UNSUPPORTED;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return HMC_ERR_UNSUPPORTED;
     const long long V = 2LL * L * L;
     if (V * Nt > kNoAllocMaxN) return HMC_ERR_UNSUPPORTED;
     void* base = nullptr;
@@ -96,7 +137,6 @@ extern "C" int hmc_cg_solve_noalloc(const double* E, int L, int Nt, const double
     v.scalars = reinterpret_cast<double*>(b + kOffScalars);
     v.bar = reinterpret_cast<unsigned*>(b + kOffBar);
     v.status = reinterpret_cast<int*>(b + kOffStatus);
-    cudaStream_t s = (cudaStream_t)stream;
     // the barrier must start at zero, the status word and the outputs clear
     if (cudaMemsetAsync(b + kOffScalars, 0, kScratchBytes - kOffScalars, s) != cudaSuccess)
         return HMC_ERR_CUDA;

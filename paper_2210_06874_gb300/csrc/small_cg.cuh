@@ -273,7 +273,7 @@ __device__ inline bool tx_wait(const Team& tm, unsigned kk, uint32_t bytes) {
         if ((n & 1023u) == 0) {
             if (t0 == 0) t0 = global_ns();
             if (team_failed(tm)) return false;
-            if (global_ns() - t0 > kWaitLimitNs) {
+            if (global_ns() - t0 > wait_limit_ns(tm.status)) {
                 set_status(tm.status, HMC_ERR_TIMEOUT);
                 return false;
             }

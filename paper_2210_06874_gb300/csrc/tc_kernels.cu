@@ -436,6 +436,7 @@ struct MixedResult {
     int reliable_updates;
     double true_res;
     int status;
+    int fp64_iterations;   // iterations of the FP64 fallback (0 if it did not run)
 };
 
 struct PersistentArgs {
@@ -449,6 +450,7 @@ struct PersistentArgs {
     double tol;
     int max_iter;
     double ru_delta;
+    int ru_every;      // reliable update after this many FP32 iterations at the latest
 };
 
 struct BatchItem {
@@ -508,6 +510,7 @@ enum SegmentEnd : int { kSegUpdate = 1, kSegMaxIter = 2, kSegNonfinite = 3 };
 struct CgScalars {
     float rr, pp, rmax, alpha, beta, sc, inv, stop, ru2;
     int it, reason;
+    int it0, every;   // iteration of the last reliable update; the most between two
 };
 
 // Thread 0, after qq = |q|^2: alpha and the scale of q.
@@ -529,7 +532,7 @@ __device__ __forceinline__ void cg_after_r(CgScalars& s, float rr_new) {
     s.it += 1;
     if (!isfinite(rr_new)) {
         rs = kSegNonfinite;
-    } else if (rr_new <= s.stop || rr_new <= s.ru2 * s.rmax) {
+    } else if (rr_new <= s.stop || rr_new <= s.ru2 * s.rmax || s.it - s.it0 >= s.every) {
         rs = kSegUpdate;
     } else {
         const float b = rr_new / s.rr;
@@ -649,10 +652,19 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
         s_cg.stop = (float)stop;
         s_cg.ru2 = (float)(pa.ru_delta * pa.ru_delta);
         s_cg.it = 0;
+        s_cg.it0 = 0;
+        s_cg.every = pa.ru_every > 0 ? pa.ru_every : 1000;
         vector_scale(rr, s_cg.sc, s_cg.inv);
     }
     __syncthreads();
     bool conv = false;
+    // progress of the FP64 true residual between reliable updates: two
+    // updates in a row that did not halve it mean the FP32 recursion has
+    // stalled (near a singular M); the rest of the solve then runs in FP64
+    double rr_last = rr_true;
+    int stalls = 0;
+    bool fallback = false;
+    res.fp64_iterations = 0;
     volatile double* seg = c.scalars + 12;   // [0] end reason, [1] iterations
     for (;;) {
         if (SMALL && in_inner) {
@@ -771,6 +783,9 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
         if (!finite_d(rr_true)) { res.status = HMC_ERR_NONFINITE; break; }
         if (rr_true <= stop) { conv = true; break; }
         if (reason == kSegMaxIter) break;
+        stalls = rr_true > 0.25 * rr_last ? stalls + 1 : 0;
+        rr_last = rr_true;
+        if (stalls >= 2) { fallback = true; break; }
         // continue from the true residual; keep the direction
         if (threadIdx.x == 0) {
             const double b = rr_true / (double)s_cg.rr;
@@ -780,12 +795,25 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
             s_cg.rmax = (float)rr_true;
             s_cg.pp = (float)pp;
             s_cg.it = it;
+            s_cg.it0 = it;
             vector_scale(pp, s_cg.sc, s_cg.inv);
         }
         __syncthreads();
         refresh = true;
     }
     res.iterations = (int)seg[1];
+    if (fallback) {
+        // FP64 CG on all CTAs from the current solution; its final true
+        // residual leaves M^dag x in q, as the reliable update does
+        f64::CgResult r64;
+        if (!f64::cg_solve(c, tm, chi, x64, pa.tol, max(1, pa.max_iter - res.iterations), r64,
+                           sm64, true))
+            return false;
+        res.fp64_iterations = r64.iterations;
+        res.true_res = r64.true_res;
+        res.status = r64.status;
+        return true;
+    }
     if (!conv && res.status == HMC_OK) res.status = HMC_ERR_CG_NOT_CONVERGED;
     res.true_res = sqrt(rr_true / chi2);
     if (!finite_d(res.true_res)) res.status = HMC_ERR_NONFINITE;
@@ -804,7 +832,7 @@ __device__ inline void cluster_begin(const PersistentArgs& pa, ClusterSync* cs, 
 __device__ __forceinline__ Team make_team(const ChainView& c) {
     Team tm;
     tm.rank = blockIdx.x;
-    tm.size = gridDim.x;
+    tm.size = gridDim.x + c.team_pad;
     tm.bar = c.bar;
     tm.status = c.status;
     tm.partials = c.partials;
@@ -861,6 +889,7 @@ __global__ void __launch_bounds__(NTHR, 1)
         c.scalars[1] = res.true_res;
         c.scalars[2] = res.status;
         c.scalars[3] = res.reliable_updates;
+        c.scalars[4] = res.fp64_iterations;
     }
     persistent_teardown<KIND == kKindSmall>(st);
     if (pa.cluster > 1) cluster_barrier_all();   // no member leaves while others may push
@@ -899,7 +928,7 @@ __device__ bool run_trajectory(const ChainView& c, Team& tm, TcState& st, f64::S
         f64::apply_team<false, f64::EPI_STORE>(c, tm, c.rho, c.chi, ea, sm64);
         ok = team_barrier(tm);
     }
-    int iters = 0, solves = 0, rus = 0, status = HMC_OK;
+    int iters = 0, solves = 0, rus = 0, fp64_iters = 0, status = HMC_OK;
     double max_res = 0.0;
     ea.phi = phi;
     ea.pi = c.pi;
@@ -941,6 +970,7 @@ __device__ bool run_trajectory(const ChainView& c, Team& tm, TcState& st, f64::S
             break;
         iters += res.iterations;
         rus += res.reliable_updates;
+        fp64_iters += res.fp64_iterations;
         ++solves;
         max_res = fmax(max_res, res.true_res);
         if (res.status != HMC_OK && status == HMC_OK) status = res.status;
@@ -990,6 +1020,7 @@ __device__ bool run_trajectory(const ChainView& c, Team& tm, TcState& st, f64::S
             c.scalars[kTrajRU] = rus;
             c.scalars[kTrajMaxRes] = max_res;
             c.scalars[kTrajStatus] = status;
+            c.scalars[kTrajFp64Iters] = fp64_iters;
         }
     }
     return ok;
@@ -1472,6 +1503,7 @@ static tc::PersistentArgs persistent_args(hmc_ctx* c, int grid, double tol, int 
         pa.tol = tol;
         pa.max_iter = max_iter;
         pa.ru_delta = c->params.ru_delta;
+        pa.ru_every = c->params.ru_every;
         pa.cluster = 0;
         pa.res_b = 0;
         pa.wide_W = 0;
@@ -1494,6 +1526,7 @@ static tc::PersistentArgs persistent_args(hmc_ctx* c, int grid, double tol, int 
         pa.tol = tol;
         pa.max_iter = max_iter;
         pa.ru_delta = c->params.ru_delta;
+        pa.ru_every = c->params.ru_every;
         pa.cluster = 0;
         pa.res_b = 0;
         return pa;
@@ -1531,6 +1564,7 @@ static tc::PersistentArgs persistent_args(hmc_ctx* c, int grid, double tol, int 
     pa.tol = tol;
     pa.max_iter = max_iter;
     pa.ru_delta = c->params.ru_delta;
+    pa.ru_every = c->params.ru_every;
     pa.cluster = 0;
     pa.res_b = res_b_ok(v, pa.mode, pa.ns_tile, pa.inner) ? 1 : 0;
     return pa;
@@ -1780,6 +1814,7 @@ int tc_batch_create(const hmc_params* p, int n, TcBatch** out) {
         it.pa.tol = c->params.cg_tol;
         it.pa.max_iter = c->params.cg_max_iter;
         it.pa.ru_delta = c->params.ru_delta;
+        it.pa.ru_every = c->params.ru_every;
         std::memset(&it.a, 0, sizeof(it.a));
         it.a.chain = (uint32_t)i;
         it.a.n_md = c->params.n_md;
@@ -1939,6 +1974,7 @@ int tc_batch_trajectory(TcBatch* b, double* phi, uint64_t seed, uint64_t traj,
         o.cg_solves = (int)v[kTrajSolves];
         o.reliable_updates = (int)v[kTrajRU];
         o.max_true_residual = v[kTrajMaxRes];
+        o.fp64_iterations = (int)v[kTrajFp64Iters];
         o.status = (int)v[kTrajStatus];
         if (o.cg_solves == 0 && o.status == HMC_OK) o.status = HMC_ERR_TIMEOUT;  // not run
         if (o.status != HMC_OK && first_bad == HMC_OK) first_bad = o.status;

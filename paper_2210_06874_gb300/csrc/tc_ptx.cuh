@@ -1,7 +1,8 @@
 // tc_ptx.cuh -- inline-PTX wrappers for the sm_103a tensor-core path:
 // mbarriers, TMA tile loads, TMEM allocation, tcgen05.mma / commit / ld.
-// Every wait is bounded: after kWaitLimitNs it records HMC_ERR_TIMEOUT in
-// the status word and returns false instead of spinning forever.
+// Every wait is bounded: after the status block's wait limit it records
+// HMC_ERR_TIMEOUT in the status word and returns false instead of spinning
+// forever.
 #pragma once
 
 #include <cuda.h>
@@ -46,7 +47,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* st
     for (uint32_t n = 1;; ++n) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((n & 63) == 0) {
-            if (global_ns() - t0 > kWaitLimitNs) {
+            if (global_ns() - t0 > wait_limit_ns(status)) {
                 set_status(status, HMC_ERR_TIMEOUT);
                 return false;
             }

@@ -49,12 +49,14 @@ class hmc_params(ctypes.Structure):
                 ("ru_delta", ctypes.c_double), ("team_ctas", ctypes.c_int),
                 ("tile_slices", ctypes.c_int), ("inner_ctas", ctypes.c_int),
                 ("operand_mode", ctypes.c_int), ("cluster_mode", ctypes.c_int),
-                ("integrator", ctypes.c_int), ("mu", ctypes.c_double)]
+                ("integrator", ctypes.c_int), ("mu", ctypes.c_double),
+                ("ru_every", ctypes.c_int)]
 
 
 class hmc_cg_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("reliable_updates", ctypes.c_int),
-                ("true_residual", ctypes.c_double), ("status", ctypes.c_int)]
+                ("true_residual", ctypes.c_double), ("status", ctypes.c_int),
+                ("fp64_iterations", ctypes.c_int)]
 
 
 class hmc_traj_out(ctypes.Structure):
@@ -62,7 +64,7 @@ class hmc_traj_out(ctypes.Structure):
                 ("u", ctypes.c_double), ("accept", ctypes.c_int),
                 ("cg_iterations", ctypes.c_int), ("cg_solves", ctypes.c_int),
                 ("reliable_updates", ctypes.c_int), ("max_true_residual", ctypes.c_double),
-                ("status", ctypes.c_int)]
+                ("status", ctypes.c_int), ("fp64_iterations", ctypes.c_int)]
 
 
 _lib = None
@@ -98,6 +100,8 @@ SIGNATURES = {
     "hmc_cg_solve_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P,
                                             ctypes.c_double, ctypes.c_int,
                                             ctypes.POINTER(hmc_cg_stats), _P]),
+    "hmc_ctx_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_double]),
+    "hmc_debug_team_padding": (ctypes.c_int, [_P, ctypes.c_int]),
 }
 
 
@@ -152,6 +156,7 @@ class Params:
     cluster_mode: int = 0
     integrator: int = 0
     mu: float = 0.0
+    ru_every: int = 0
 
     @property
     def V(self):
@@ -166,7 +171,7 @@ class Params:
                           self.traj_length, self.cg_tol, self.cg_max_iter, self.precision,
                           self.ru_delta, self.team_ctas, self.tile_slices,
                           self.inner_ctas, self.operand_mode, self.cluster_mode,
-                          self.integrator, self.mu)
+                          self.integrator, self.mu, self.ru_every)
 
 
 class Context:
@@ -277,6 +282,16 @@ class Context:
                                                  ctypes.byref(out), _stream()))
         return out.value
 
+    def set_wait_limit(self, seconds):
+        """Time limit of every bounded device wait of later launches (0: the
+        default, 20 s)."""
+        _check("hmc_ctx_set_wait_limit", self.lib.hmc_ctx_set_wait_limit(self._h, seconds))
+
+    def debug_team_padding(self, extra_ctas):
+        """Testing only: team barriers of later launches expect extra_ctas
+        CTAs beyond those launched, so their bounded waits run out."""
+        _check("hmc_debug_team_padding", self.lib.hmc_debug_team_padding(self._h, extra_ctas))
+
     def trajectory(self, phi, seed, traj_index, chain=0, allow_not_converged=False):
         self._field(phi, "phi", torch.float64)
         out = hmc_traj_out()
@@ -380,11 +395,32 @@ def rng_draw(seed, stream_id, traj, chain, n, device=None):
     return raw, z0, z1
 
 
+def check_noalloc_args(E, L, Nt, phi, chi, x, device):
+    """Argument checks of cg_solve_noalloc, made before the library is called:
+    E float64 [V, V], phi float64 [Nt, V], chi and x complex128 [Nt, V], all
+    contiguous tensors on `device`, x not overlapping chi.  Raises ValueError."""
+    if not (isinstance(L, int) and isinstance(Nt, int)) or L < 1 or Nt < 1:
+        raise ValueError("L and Nt must be positive integers")
+    V = 2 * L * L
+    want = {"E": (E, torch.float64, (V, V)), "phi": (phi, torch.float64, (Nt, V)),
+            "chi": (chi, torch.complex128, (Nt, V)), "x": (x, torch.complex128, (Nt, V))}
+    for name, (t, dt, shape) in want.items():
+        if not isinstance(t, torch.Tensor) or t.dtype != dt or tuple(t.shape) != shape \
+                or not t.is_contiguous() or t.device != device:
+            raise ValueError("%s must be a contiguous %s tensor of shape %s on %s"
+                             % (name, dt, shape, device))
+    if x.data_ptr() < chi.data_ptr() + chi.numel() * chi.element_size() and \
+            chi.data_ptr() < x.data_ptr() + x.numel() * x.element_size():
+        raise ValueError("x must not overlap chi")
+
+
 def cg_solve_noalloc(E, L, Nt, phi, chi, x, tol, max_iter):
     """hmc_cg_solve_noalloc: FP64 CG with the library's static scratch (no
     device allocation inside the call).  E: float64 [V, V], phi: float64
     [Nt, V], chi and x: complex128 [Nt, V], all contiguous on the current
-    device; x is written.  Returns (code, hmc_cg_stats)."""
+    CUDA device; x is written.  Returns (code, hmc_cg_stats)."""
+    check_noalloc_args(E, L, Nt, phi, chi, x,
+                       torch.device("cuda", torch.cuda.current_device()))
     lib = load_library()
     st = hmc_cg_stats()
     code = lib.hmc_cg_solve_noalloc(_ptr(E), L, Nt, _ptr(phi), _ptr(chi), _ptr(x), tol,

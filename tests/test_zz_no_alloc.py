@@ -1,7 +1,9 @@
 """hmc_cg_solve_noalloc: the FP64 CG for callers that may not allocate device
-memory (graph capture, pool-managed or fixed-budget hosts).  It must give the
-result of hmc_cg_solve with HMC_PREC_FP64, call after call, while its scratch
-sits in the library's static device array.  Collected last on purpose."""
+memory (hosts whose device memory comes from a framework pool or a fixed
+budget, plugins barred from growing the heap).  It must give the result of
+hmc_cg_solve with HMC_PREC_FP64, call after call, while its scratch sits in
+the library's static device array; on a stream under graph capture it must
+refuse before enqueuing anything.  Collected last on purpose."""
 import pytest
 import torch
 
@@ -35,9 +37,34 @@ def test_noalloc_matches_cg_solve_twice(L, Nt, beta, U):
 def test_noalloc_rejects_oversize():
     L, Nt = 24, 96                           # V * Nt = 110592 > 32768
     V = 2 * L * L
-    E = torch.zeros((8, 8), dtype=torch.float64, device=DEV)
+    E = torch.zeros((V, V), dtype=torch.float64, device=DEV)
     phi = torch.zeros((Nt, V), dtype=torch.float64, device=DEV)
     chi = torch.zeros((Nt, V), dtype=torch.complex128, device=DEV)
     x = torch.zeros_like(chi)
     code, _ = hmc.cg_solve_noalloc(E, L, Nt, phi, chi, x, 1e-10, 10)
     assert code == hmc.HMC_ERR_UNSUPPORTED
+
+
+def test_noalloc_refuses_graph_capture():
+    """The call synchronises and reads its result on the host, so it cannot
+    be captured: under capture it returns HMC_ERR_UNSUPPORTED and leaves the
+    capture valid (the work captured around it replays)."""
+    L, Nt = 3, 8
+    V = 2 * L * L
+    ctx = hmc.Context(hmc.Params(L=L, Nt=Nt, beta=2.0, U=2.0))
+    E = ctx.transfer_matrix().to(DEV)
+    phi = torch.from_numpy(synth.gaussian_field(43, Nt, V, 0.5, scale=0.5)).to(DEV)
+    chi = torch.from_numpy(synth.complex_gaussian(44, Nt, V)).to(DEV)
+    x = torch.zeros_like(chi)
+    code, _ = hmc.cg_solve_noalloc(E, L, Nt, phi, chi, x, 1e-12, 100000)   # set-up, uncaptured
+    assert code == hmc.HMC_OK
+    y = torch.zeros(4, device=DEV)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        y.add_(1.0)
+        code, st = hmc.cg_solve_noalloc(E, L, Nt, phi, chi, x, 1e-12, 100000)
+        y.add_(2.0)
+    assert code == hmc.HMC_ERR_UNSUPPORTED
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(y, torch.full_like(y, 3.0))

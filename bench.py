@@ -2,9 +2,14 @@
 
 One step = one HMC trajectory (heat bath, chi = M rho, n_md + 1 CG solves
 with forces, leapfrog, Metropolis) of the chosen workload, run by
-hmc_trajectory as one persistent launch.  Default workload: L=6 (72 sites),
-Nt=32, U=3.5, beta=4, 20 leapfrog steps over tau=1, thermalised from a cold
-start by untimed trajectories.
+hmc_trajectory as one persistent launch.  Default workload: the largest
+single-GPU configuration, L=24 (1152 sites), Nt=96, U=4, beta=12, 30
+leapfrog steps over tau=1, mixed precision (FP16-split tensor-core
+contraction, FP32 CG with FP64 reliable updates), thermalised from a cold
+start by untimed trajectories.  The same line carries the plain FP64 GPU
+path on the same field and pseudofermion source (per solve, scaled to a
+trajectory), M-applications/s with their tensor-core and HBM roofline
+fractions, and the oracle on the host cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
                     [--precision fp64|mixed] [--impl ours|reference]
@@ -27,20 +32,19 @@ sys.path.insert(0, ROOT)
 METRIC = ("HMC trajectories/s and M-applications/s (frac. of roofline), "
           "mixed vs FP64 at equal tol")
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# dram__bytes_read.sum + dram__bytes_write.sum of one trajectory launch in the
-# CUDA-core cluster mode, by (workload, cluster size), from ncu
-CAPTURED_TRAFFIC = {("l6_nt32", 16): 764420}
-# FP32 FMA peak of the whole GPU from unit counts and the maximum SM clock
-FP32_FMA_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+PROFILES = os.path.join(ROOT, "profiles")
+CSRC = os.path.join(ROOT, "paper_2210_06874_gb300", "csrc")
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# untimed trajectories from the cold start before the warm-up ones
+THERM = {"l3_nt8": 0, "l6_nt32": 20, "l12_nt64": 10, "l24_nt96": 5}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="l6_nt32")
+    ap.add_argument("--workload", default="l24_nt96")
     ap.add_argument("--integrator", default="leapfrog", choices=["leapfrog", "omelyan"],
                     help="trajectory mode: molecular-dynamics integrator (the workload's "
                          "configuration is leapfrog)")
@@ -65,10 +69,13 @@ def parse():
     ap.add_argument("--therm", type=int, default=None,
                     help="untimed thermalisation trajectories before warm-up")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-arm", action="store_true",
+                    help="trajectory mode, mixed: skip the plain FP64 GPU path's solve")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
-    ap.add_argument("--operand-mode", type=int, default=None, choices=[0, 1, 2, 3, 4],
-                    help="apply mode: operand_mode of the mixed path (default: the "
-                         "workload's; 1 site-major tiles, 4 slice-major tiles)")
+    ap.add_argument("--operand-mode", type=int, default=None, choices=[0, 1, 2, 3, 4, 5],
+                    help="operand_mode of the mixed path instead of the autotuner's choice "
+                         "(1 site-major tiles, 3 CUDA-core cluster mode, 4 slice-major "
+                         "tiles, 5 split-K tiles with E resident)")
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     return ap.parse_args()
 
@@ -172,6 +179,48 @@ def flops_per_apply(V, Nt):
 
 
 
+def fp32_fma_tflops(torch, dev):
+    """FP32 FMA peak of the whole GPU from unit counts: SMs (device
+    attribute) x 128 FP32 lanes x 2 flop x the maximum SM clock."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks, _ = load_peaks()
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, sms, mhz
+
+
+def sources_sha():
+    """Hash of the library's CUDA sources (the counters of a profile are only
+    valid for the kernels they were taken on)."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(CSRC, "*"))):
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(workload, key):
+    """DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per unit
+    recorded by a committed ncu summary under profiles/ for this workload, as
+    a line `traffic <workload> <key> <bytes> sources <sha>`; None when there
+    is none or the kernels changed since (the sha of csrc/ differs)."""
+    import glob
+    import re
+    sha = sources_sha()
+    pat = re.compile(r"^traffic\s+(\S+)\s+(\S+)\s+([0-9.eE+]+)\s+sources\s+([0-9a-f]+)")
+    for f in sorted(glob.glob(os.path.join(PROFILES, "*.md"))):
+        with open(f) as fh:
+            for ln in fh:
+                m = pat.match(ln.strip().strip("`"))
+                if m and m.group(1) == workload and m.group(2) == key:
+                    if m.group(4) != sha:
+                        return None, "%s: kernels changed since the capture" % os.path.basename(f)
+                    return float(m.group(3)), os.path.basename(f)
+    return None, "no committed capture for this workload"
+
+
 def flush_l2(buf, acc):
     """Evict the L2 between timed regions: a write larger than the L2, then a
     read sweep of it, so the L2 holds clean lines and the timed work pays
@@ -234,6 +283,65 @@ def cpu_oracle_rate(name, prec, sample_s, phi_np=None, integrator="leapfrog", n_
             "kind": "oracle",
             "sample": "%d oracle trajectories of %s (%d CG iterations), %.1f s; NumPy FP64, "
                       "BLAS threads as configured" % (n, name, iters, dt)}
+
+
+def cpu_oracle_cg_iter_time(name, phi_np, chi_np, sample_s):
+    """Seconds per FP64 CG iteration of the oracle (as it stands) on the
+    workload's lattice: its cg_solve from x0 = 0 on (phi, chi), capped at as
+    many iterations as fit in about sample_s seconds (a short first run
+    sizes the cap).  Returns (seconds per iteration, iterations timed, s)."""
+    from oracle import hmc as ohmc, lattice, operators as ops
+    from paper_2210_06874_gb300 import synth
+    w = synth.WORKLOADS[name]
+    delta = w["beta"] / w["Nt"]
+    E = ops.transfer_matrix(lattice.hopping_matrix(w["L"]), delta * w["kappa"])
+    t0 = time.perf_counter()
+    _, it0, _ = ohmc.cg_solve(E, phi_np, chi_np, tol=1e-300, max_iter=3)
+    per = (time.perf_counter() - t0) / max(it0, 1)
+    cap = max(3, int(sample_s / per))
+    t0 = time.perf_counter()
+    _, it, _ = ohmc.cg_solve(E, phi_np, chi_np, tol=1e-300, max_iter=cap)
+    dt = time.perf_counter() - t0
+    return dt / max(it, 1), it, dt
+
+
+def cpu_oracle_rate_by_iterations(name, phi_np, chi_np, sample_s, iters_per_solve, n_solves,
+                                  single_thread=False):
+    """Oracle trajectories/s for workloads whose trajectory takes the oracle
+    minutes: seconds per FP64 CG iteration, timed on a bounded sample, times
+    the FP64 CG iterations of one trajectory (n_solves solves of
+    iters_per_solve iterations from x0 = 0, the oracle's own algorithm)."""
+    if single_thread:
+        import tempfile
+        import numpy as np
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+                   MKL_NUM_THREADS="1", BLIS_NUM_THREADS="1")
+        fd, path = tempfile.mkstemp(suffix=".npz")
+        os.close(fd)
+        np.savez(path, phi=phi_np, chi=chi_np)
+        code = ("import json, sys, numpy as np; sys.path.insert(0, %r); import bench; "
+                "d = np.load(%r); print(json.dumps(bench.cpu_oracle_cg_iter_time(%r, d['phi'], "
+                "d['chi'], %r)))" % (ROOT, path, name, sample_s))
+        try:
+            r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True,
+                               text=True, timeout=sample_s * 10 + 120)
+            per, it, dt = json.loads(r.stdout.strip().splitlines()[-1])
+        except Exception as e:   # a reporting extra: never fail the bench on it
+            return {"unavailable": str(e)[:200]}
+        finally:
+            os.unlink(path)
+        cores, how = 1, "one thread"
+    else:
+        per, it, dt = cpu_oracle_cg_iter_time(name, phi_np, chi_np, sample_s)
+        cores, how = os.cpu_count(), "BLAS threads as configured"
+    total = iters_per_solve * n_solves
+    return {"value": 1.0 / (per * total), "unit": "trajectories/s", "cores": cores,
+            "kind": "oracle", "cg_iterations_per_s": 1.0 / per,
+            "sample": "%d FP64 CG iterations of the oracle on %s (%.1f s, %.2f ms each), "
+                      "scaled to one trajectory of %d solves x %d iterations from x0 = 0 "
+                      "(the plain FP64 GPU path's count on the same field and source, "
+                      "the oracle's algorithm); NumPy FP64, %s"
+                      % (it, name, dt, 1e3 * per, n_solves, iters_per_solve, how)}
 
 
 def cpu_oracle_rate_single_thread(name, prec, sample_s, phi_np=None, integrator="leapfrog",
@@ -323,6 +431,29 @@ def cpu_oracle_batch_rate(n_chains, sample_s):
 
 
 # ----------------------------------------------------------------- reference arm
+def reference_iteration_setup(name, args):
+    """For workloads whose oracle trajectory takes minutes to hours: the
+    start field, the heat-bath source chi = M rho of its first solve, and the
+    oracle's own CG iteration count for that solve (x0 = 0, the workload's
+    tolerance).  The steps then time oracle CG iterations and scale them by
+    that count: the first solve from the start field is the cheapest of the
+    chain, so the estimate favours the oracle."""
+    import math
+    from oracle import hmc as ohmc, lattice, operators as ops
+    from paper_2210_06874_gb300 import synth
+    w = synth.WORKLOADS[name]
+    delta = w["beta"] / w["Nt"]
+    V = 2 * w["L"] ** 2
+    E = ops.transfer_matrix(lattice.hopping_matrix(w["L"]), delta * w["kappa"])
+    phi = synth.start_field(name)
+    rho = synth.complex_gaussian(w["seed"] + 77, w["Nt"], V) / math.sqrt(2.0)
+    chi = ops.apply_M(E, phi, rho)
+    _, iters, _ = ohmc.cg_solve(E, phi, chi, tol=w["cg_tol"], max_iter=200000)
+    n_md = args.n_md or w["n_md"]
+    n_solves = (2 * n_md if args.integrator == "omelyan" else n_md) + 1
+    return phi, chi, iters, n_solves
+
+
 def run_reference(args):
     """The oracle as it stands, on the host cores, for the workload and
     metric of our arm: trajectories/s (single chain or the batched chains)
@@ -341,6 +472,9 @@ def run_reference(args):
         return
     batch = name.startswith("batch")
     apply = args.mode == "apply" and not batch
+    by_iters = None
+    if not batch and not apply and 2 * synth.WORKLOADS[name]["L"] ** 2 >= 288:
+        by_iters = reference_iteration_setup(name, args)
     rates, samples, secs = [], [], []
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -348,6 +482,13 @@ def run_reference(args):
             r = cpu_oracle_batch_rate(args.chains, sample_s)
         elif apply:
             r = cpu_oracle_apply_rate(name, sample_s)
+        elif by_iters:
+            phi0, chi0, iters0, n_solves = by_iters
+            r = cpu_oracle_rate_by_iterations(name, phi0, chi0, sample_s, iters0, n_solves)
+            r["sample"] = r["sample"].replace(
+                "(the plain FP64 GPU path's count on the same field and source, the oracle's "
+                "algorithm)", "(the oracle's own count for the first solve from the workload's "
+                "start field, the cheapest solve of the chain)")
         else:
             r = cpu_oracle_rate(name, None, sample_s, integrator=args.integrator,
                                 n_md=args.n_md)
@@ -383,6 +524,37 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------- our arm
+def fp64_vs_mixed_solve(ctx, params, phi, seed, dev):
+    """The plain FP64 GPU path against the mixed path on one pseudofermion
+    solve of the current field: chi = M rho with rho ~ exp(-rho^dag rho)
+    (the heat bath's source), both solves from x0 = 0 to the workload's
+    tolerance, timed with CUDA events on the current stream."""
+    import math
+    import torch
+    from paper_2210_06874_gb300 import hmc, synth
+    V, Nt = params.V, params.Nt
+    rho = torch.from_numpy(synth.complex_gaussian(seed + 77, Nt, V) / math.sqrt(2.0)).to(dev)
+    chi = ctx.apply_M(phi, rho, prec=hmc.PREC_FP64)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, prec in (("mixed", hmc.PREC_MIXED), ("fp64", hmc.PREC_FP64)):
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        x, st = ctx.cg_solve(phi, chi, tol=params.cg_tol, max_iter=params.cg_max_iter,
+                             prec=prec, allow_not_converged=True)
+        e.record(stream)
+        e.synchronize()
+        res[name] = {"ms": s.elapsed_time(e), "iterations": st.iterations,
+                     "reliable_updates": st.reliable_updates,
+                     "true_residual": st.true_residual, "status": st.status, "x": x}
+    xm, x64 = res["mixed"].pop("x"), res["fp64"].pop("x")
+    res["solution_rel_diff"] = float(torch.linalg.vector_norm(xm - x64) /
+                                     torch.linalg.vector_norm(x64))
+    res["chi"] = chi
+    return res
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -400,9 +572,13 @@ def run_ours(args):
         params.n_md = args.n_md
     params.integrator = 1 if args.integrator == "omelyan" else 0
     tuned = None
+    if prec == "mixed" and args.operand_mode is not None:
+        params.operand_mode = args.operand_mode
     if prec == "mixed" and not args.no_tune:
         from paper_2210_06874_gb300 import autotune
-        params = autotune.tune_ru(autotune.tune(params))
+        if args.operand_mode is None:
+            params = autotune.tune(params)
+        params = autotune.tune_ru(params)
         tuned = {"team_ctas": params.team_ctas, "inner_ctas": params.inner_ctas,
                  "tile_slices": params.tile_slices, "operand_mode": params.operand_mode,
                  "ru_delta": params.ru_delta}
@@ -411,7 +587,7 @@ def run_ours(args):
     dev = torch.device("cuda", local_rank)
     phi = torch.from_numpy(synth.start_field(name)).to(dev)
     seed = w["seed"]
-    n_therm = args.therm if args.therm is not None else (0 if w["start"] == "gaussian" else 20)
+    n_therm = args.therm if args.therm is not None else THERM.get(name, 10)
     traj = 0
     for _ in range(n_therm + args.warmup):
         ctx.trajectory(phi, seed, traj, rank, allow_not_converged=True)
@@ -466,33 +642,49 @@ def run_ours(args):
     h2d = Nt * V * 8
     d2h = Nt * V * 8 + 8 * 16
 
+    # the plain FP64 GPU path on the same field and source (mixed runs only)
+    n_solves = (2 * params.n_md if params.integrator == 1 else params.n_md) + 1
+    cmp = None
+    if prec == "mixed" and not args.no_fp64_arm:
+        cmp = fp64_vs_mixed_solve(ctx, params, phi, seed, dev)
+    chi_np = cmp.pop("chi").cpu().numpy() if cmp else None
+
     # roofline of the dominant (only) kernel: the persistent trajectory launch
     peaks, peaks_kind = load_peaks()
     mean_iters = statistics.mean(o.cg_iterations for o in outs)
     n_app = statistics.mean(applies_per_traj(o, params.n_md) for o in outs)
     flop = n_app * flops_per_apply(V, Nt)
+    byts = n_app * apply_bytes(V, Nt, prec)
     achieved = flop / (ms_per_step * 1e-3) / 1e12
+    hbm_peak = peaks.get("hbm_gbs", FALLBACK["hbm_gbs"])
+    traffic_it, traffic_src = committed_traffic(name, "per-cg-iteration")
+    traffic = traffic_it * mean_iters if traffic_it is not None else None
+    hbm = {"achieved_gbs": byts / (ms_per_step * 1e-3) / 1e9, "peak_gbs": hbm_peak,
+           "algorithmic_bytes": byts,
+           "bytes_per_application": apply_bytes(V, Nt, prec),
+           "peak_source": "%s STREAM-style copy" % peaks_kind}
+    hbm["frac"] = hbm["achieved_gbs"] / hbm_peak
     if prec == "fp64":
         peak = measure_dgemm_tflops(torch)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
                 "peak_source": "measured cuBLAS DGEMM 4096^3 on this GPU (FP64 ALU peak)"}
     elif params.operand_mode == 3:
-        peak = FP32_FMA_TFLOPS
-        # DRAM bytes of one k_trajectory<1> launch from the ncu capture in
-        # profiles/k_trajectory_small_l6_nt32_full.md (that workload and
-        # cluster size only; null elsewhere)
-        traffic = (CAPTURED_TRAFFIC.get((name, params.inner_ctas))
-                   if params.team_ctas == params.inner_ctas else None)
+        peak, sms, mhz = fp32_fma_tflops(torch, dev)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "peak_source": "FP32 FMA rate from unit counts: 152 SMs x 128 lanes x 2 flop "
-                               "x 2.07 GHz (the CUDA-core cluster mode runs on one cluster)"}
+                "peak_source": "FP32 FMA rate from unit counts: %d SMs (device attribute) x "
+                               "128 lanes x 2 flop x %.0f MHz (the CUDA-core cluster mode runs "
+                               "on one cluster)" % (sms, mhz)}
     else:
         peak = peaks.get("bf16_tflops_sustained", FALLBACK["bf16_tflops_sustained"])
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
                 "peak_source": "%s bf16 dense sustained (fp16 has the same rate)" % peaks_kind}
+    roof["flop_per_application"] = flops_per_apply(V, Nt)
+    roof["applications_per_launch"] = n_app
+    roof["traffic_source"] = traffic_src
+    roof["hbm"] = hbm
     line = {
         "metric": METRIC, "value": value, "unit": "trajectories/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -510,6 +702,7 @@ def run_ours(args):
                    "launch_shape": tuned or "automatic"},
         "m_applications_per_s": world * n_app / (ms_per_step * 1e-3),
         "cg_iterations_per_traj": mean_iters,
+        "cg_iterations_per_s": world * mean_iters / (ms_per_step * 1e-3),
         "acceptance": statistics.mean(o.accept for o in outs),
         "mean_abs_dH": statistics.mean(abs(o.dH) for o in outs),
         "max_true_residual": max(o.max_true_residual for o in outs),
@@ -520,13 +713,33 @@ def run_ours(args):
         "clocks": clk,
         "wall_s_timed_region": wall,
     }
+    if cmp:
+        t64 = cmp["fp64"]["ms"] * 1e-3 * n_solves
+        cmp["fp64_trajectories_per_s_est"] = 1.0 / t64
+        cmp["mixed_over_fp64_trajectories"] = value / world * t64
+        cmp["mixed_over_fp64_solve"] = cmp["fp64"]["ms"] / cmp["mixed"]["ms"]
+        cmp["how"] = ("one solve of the thermalised field's heat-bath source chi = M rho from "
+                      "x0 = 0 on each path, same tolerance; the FP64 trajectory estimate is "
+                      "%d such solves (the plain FP64 trajectory starts every solve from zero)"
+                      % n_solves)
+        line["fp64_arm"] = cmp
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_oracle_rate(name, prec, args.cpu_sample_s,
-                                               phi_np=phi.cpu().numpy(),
-                                               integrator=args.integrator, n_md=params.n_md)
-        line["cpu_baseline"]["single_thread"] = cpu_oracle_rate_single_thread(
-            name, prec, min(args.cpu_sample_s, 10.0), phi_np=phi.cpu().numpy(),
-            integrator=args.integrator, n_md=params.n_md)
+        phi_np = phi.cpu().numpy()
+        if V >= 288 and cmp:
+            # an oracle trajectory takes minutes to hours here: time its CG
+            # iterations on a bounded sample and count them by the FP64 path
+            line["cpu_baseline"] = cpu_oracle_rate_by_iterations(
+                name, phi_np, chi_np, args.cpu_sample_s, cmp["fp64"]["iterations"], n_solves)
+            line["cpu_baseline"]["single_thread"] = cpu_oracle_rate_by_iterations(
+                name, phi_np, chi_np, min(args.cpu_sample_s, 10.0), cmp["fp64"]["iterations"],
+                n_solves, single_thread=True)
+        else:
+            line["cpu_baseline"] = cpu_oracle_rate(name, prec, args.cpu_sample_s,
+                                                   phi_np=phi_np, integrator=args.integrator,
+                                                   n_md=params.n_md)
+            line["cpu_baseline"]["single_thread"] = cpu_oracle_rate_single_thread(
+                name, prec, min(args.cpu_sample_s, 10.0), phi_np=phi_np,
+                integrator=args.integrator, n_md=params.n_md)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -51,7 +51,7 @@ def bad(**kw):
 @pytest.mark.parametrize("field,value", [("L", 0), ("Nt", 0), ("U", 0.0), ("beta", -1.0),
                                          ("n_md", 0), ("cg_tol", 0.0), ("cg_max_iter", 0),
                                          ("precision", 7), ("ru_delta", 1.5),
-                                         ("L", 30000), ("operand_mode", 5),
+                                         ("L", 30000), ("operand_mode", 6),
                                          ("cluster_mode", 3), ("cluster_mode", -1),
                                          ("integrator", 2), ("integrator", -1),
                                          ("mu", float("nan")), ("mu", 100.0),

@@ -140,13 +140,13 @@ static int valid_params(const hmc_params* p) {
     if (p->ru_delta < 0.0 || p->ru_delta >= 1.0) return 0;
     if (p->team_ctas < 0 || p->team_ctas > 1024) return 0;
     if (p->inner_ctas < 0 || p->inner_ctas > 1024) return 0;
-    if (p->operand_mode < 0 || p->operand_mode > 4) return 0;
+    if (p->operand_mode < 0 || p->operand_mode > 5) return 0;
     if (p->cluster_mode < 0 || p->cluster_mode > 2) return 0;
     if (p->integrator < 0 || p->integrator > 1) return 0;
     if (p->ru_every < 0) return 0;
     // |delta mu| <= 5: the scaled E keeps its FP16 split in range
     if (!std::isfinite(p->mu) || std::fabs(p->mu * p->beta / p->Nt) > 5.0) return 0;
-    if (p->operand_mode == 4) {
+    if (p->operand_mode == 4 || p->operand_mode == 5) {
         if (p->tile_slices < 0 || p->tile_slices > 64) return 0;
     } else if (p->tile_slices != 0 && p->tile_slices != 8 && p->tile_slices != 16 &&
                p->tile_slices != 32) {

@@ -31,6 +31,10 @@ struct ChainView {
     double *pi, *phi_old;       // double [Nt][V]
     // FP32 workspaces for the mixed path, float2 [Nt][V] each
     float2 *cis_f, *r_f, *p_f, *p2_f, *q_f, *x_f;
+    // split-K CG (operand_mode 5): G = E p' carried per target slice, and
+    // u = e^{i phi} q, the source of the M application
+    float2 *g_f, *u_f;
+    unsigned long long* gslots; // sequence-numbered partial sums and totals (tc_splitk.cuh)
     // team synchronisation
     unsigned* bar;              // 2 words
     int* status;                // device status block (kStatusBlockBytes): status

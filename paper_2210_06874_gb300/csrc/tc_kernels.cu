@@ -14,6 +14,7 @@
 #include "tc_path.h"
 #include "tc_tile.cuh"
 #include "tc_wide.cuh"
+#include "tc_splitk.cuh"
 #include "small_cg.cuh"
 
 namespace hmc {
@@ -36,6 +37,8 @@ struct TcCtx {
     // pre-split U (plain remainder) over bhi / blo with 128-row boxes
     CUtensorMap map_whi, map_wlo, map_uhi, map_ulo;
     int w_cg, w_apply, ns_wapply, csplit_apply;
+    // split-K tiles (operand_mode 5): the scaled split of E in 128-row boxes
+    CUtensorMap map_shi, map_slo;
 };
 
 namespace tc {
@@ -451,6 +454,7 @@ struct PersistentArgs {
     int max_iter;
     double ru_delta;
     int ru_every;      // reliable update after this many FP32 iterations at the latest
+    int sk_C;          // kSplitK: CTAs per cluster splitting K (ns_tile: slices per n-group)
 };
 
 struct BatchItem {
@@ -544,9 +548,86 @@ __device__ __forceinline__ void cg_after_r(CgScalars& s, float rr_new) {
     s.reason = rs;
 }
 
+// FP32 CG iterations of one segment (until a reliable update, max_iter or
+// a non-finite norm) on split-K tiles with E' resident: M^dag contracts r
+// (G = E r + beta G carried by the owners), M contracts u = e^{i phi} q.
+// The owner vectors live in shared memory for the segment: r is loaded from
+// the FP32 residual (or, refresh, the FP64 residual, also written back as
+// FP32), p and G start at zero in the first segment of a solve and carry
+// over otherwise, x (the FP32 increment) starts at zero and is folded into
+// x64 by its owner at the end.  Returns the segment's end reason, or -1 if
+// a bounded wait failed.  Not inlined into the persistent kernels: the
+// iteration gets its own register budget.
+__device__ __noinline__ int sk_segment(const ChainView& c, Team& ti, TcState& st,
+                                       const PersistentArgs& pa, ClusterSync* ics,
+                                       CgScalars& s_cg, bool refresh, bool first,
+                                       const float2* cisf, double2* x64) {
+    int reason = kSegMaxIter;
+    const SkGeom g = sk_geom(ti.rank, pa.sk_C, pa.ns_tile, c.V, c.Nt, c.Vr, c.Vp);
+    Team tcl = ti;
+    tcl.rank = g.rank;
+    tcl.size = g.C;
+    tcl.cs = ics;
+    SkOwner ow;
+    ow.init(st.base, g);
+    float2* rf = c.r_f;
+    HMC_SK_OWNED(o, oi, g, c) {
+        float2 rv;
+        if (refresh) {
+            const double2 d = c.r[o];
+            rv = make_float2((float)d.x, (float)d.y);
+            rf[o] = rv;
+        } else {
+            rv = rf[o];
+        }
+        ow.r[oi] = rv;
+        ow.x[oi] = make_float2(0.f, 0.f);
+        if (first) {
+            ow.p[oi] = make_float2(0.f, 0.f);
+            ow.G[oi] = make_float2(0.f, 0.f);
+        }
+    }
+    __syncthreads();
+    while (s_cg.it < pa.max_iter) {
+        float scr, invr;
+        vector_scale_f(s_cg.rr, scr, invr);
+        SkSrc sr{rf, c.r, refresh, c.V};
+        SkEpiDag ed{ow, c.u_f, cisf, s_cg.beta, c.V, c.Nt, 0.f};
+        if (!sk_apply<true>(st, g, tcl, sr, c.V, c.Nt, scr, invr * c.e_inv, ed)) return -1;
+        float qq;
+        if (!gather_sum_f(ti, c.gslots, st.gseq, ed.acc, qq)) return -1;
+        refresh = false;
+        if (threadIdx.x == 0) cg_after_q(s_cg, qq);
+        __syncthreads();
+        if (s_cg.reason != 0) { reason = s_cg.reason; break; }
+        SkSrc su{c.u_f, nullptr, false, c.V};
+        SkEpiM em{ow, rf, s_cg.alpha, c.V, 0.f};
+        if (!sk_apply<false>(st, g, tcl, su, c.V, c.Nt, s_cg.sc, s_cg.inv * c.e_inv, em))
+            return -1;
+        float rr_new;
+        if (!gather_sum_f(ti, c.gslots, st.gseq, em.acc, rr_new)) return -1;
+        if (threadIdx.x == 0) {
+            cg_after_r(s_cg, rr_new);
+            if (s_cg.reason == 0 && s_cg.it >= pa.max_iter) s_cg.reason = kSegMaxIter;
+        }
+        __syncthreads();
+        if (s_cg.reason != 0) { reason = s_cg.reason; break; }
+    }
+    if (reason != kSegNonfinite) {
+        HMC_SK_OWNED(o, oi, g, c) {
+            const float2 d = ow.x[oi];
+            double2 xv = x64[o];
+            xv.x += (double)d.x;
+            xv.y += (double)d.y;
+            x64[o] = xv;
+        }
+    }
+    return reason;
+}
+
 // Kernel kinds of the FP32 iterations: site-major tensor-core tiles, the
 // CUDA-core cluster solver, slice-major tensor-core tiles.
-enum TileKind : int { kKindSite = 0, kKindSmall = 1, kKindSlice = 2 };
+enum TileKind : int { kKindSite = 0, kKindSmall = 1, kKindSlice = 2, kKindSplitK = 3 };
 
 template <int KIND>
 __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& sm64,
@@ -612,6 +693,25 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
         if (!team_sum<1>(ti, v2)) return false;
         rr = v2[0];
       }
+    } else if (KIND == kKindSplitK && in_inner) {
+        // split-K: this CTA's part of E' stays resident for the whole launch
+        if (!st.sk_loaded) {
+            const SkGeom g = sk_geom(tm.rank, pa.sk_C, pa.ns_tile, c.V, c.Nt, c.Vr, c.Vp);
+            if (!sk_load_E(st, g, mhi, mlo)) return false;
+            st.sk_loaded = 1;
+        }
+        double v2[1] = {0.0};
+        HMC_TEAM_ELEMS(e, c, ti) {
+            const double2 ch = r0[e];
+            const float2 rv = make_float2((float)ch.x, (float)ch.y);
+            rf[e] = rv;
+            pf[e] = make_float2(0.f, 0.f);
+            xf[e] = make_float2(0.f, 0.f);
+            c.g_f[e] = make_float2(0.f, 0.f);
+            v2[0] += (double)rv.x * rv.x + (double)rv.y * rv.y;
+        }
+        if (!team_sum<1>(ti, v2)) return false;
+        rr = v2[0];
     } else if (in_inner) {
         if (pa.mode == kResident) {
             if (!tc_load_resident(st, mhi, mlo, (tm.rank % (c.Vr / TM)) * TM, c.Vp / KCH))
@@ -658,6 +758,7 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
     }
     __syncthreads();
     bool conv = false;
+    bool sk_first = true;   // split-K: the first segment starts p and G at zero
     // progress of the FP64 true residual between reliable updates: two
     // updates in a row that did not halve it mean the FP32 recursion has
     // stalled (near a singular M); the rest of the solve then runs in FP64
@@ -714,6 +815,15 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
             }
             if (threadIdx.x == 0 && ti.cs) ti.cs->count_tx = kk;
             if (reason != kSegNonfinite) small_fold_x(sm, x64);
+            if (tm.rank == 0 && threadIdx.x == 0) {
+                seg[0] = reason;
+                seg[1] = s_cg.it;
+            }
+        } else if (KIND == kKindSplitK && in_inner) {
+            const int reason = sk_segment(c, ti, st, pa, ics, s_cg, refresh, sk_first, cisf, x64);
+            if (reason < 0) return false;
+            refresh = false;
+            sk_first = false;
             if (tm.rank == 0 && threadIdx.x == 0) {
                 seg[0] = reason;
                 seg[1] = s_cg.it;
@@ -1289,6 +1399,10 @@ int tc_ctx_init(hmc_ctx* c) {
     v.p2_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
     v.q_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
     v.x_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
+    v.g_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
+    v.u_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
+    v.gslots = (unsigned long long*)dev_alloc(c, tc::kGatherSlots * sizeof(unsigned long long),
+                                              &ok);
     if (!ok) return HMC_ERR_CUDA;
     if (cudaMemcpy(dhi, hi.data(), hi.size() * sizeof(__half), cudaMemcpyHostToDevice) !=
             cudaSuccess ||
@@ -1304,7 +1418,8 @@ int tc_ctx_init(hmc_ctx* c) {
     v.Ew_hi = dwhi;
     v.Ew_lo = dwlo;
     c->tc = new TcCtx();
-    if (!make_map(&c->tc->map_hi, dhi, v.Vr, v.Vp) || !make_map(&c->tc->map_lo, dlo, v.Vr, v.Vp))
+    if (!make_map(&c->tc->map_hi, dhi, v.Vr, v.Vp) || !make_map(&c->tc->map_lo, dlo, v.Vr, v.Vp) ||
+        !make_map(&c->tc->map_shi, dwhi, v.Vr, v.Vp) || !make_map(&c->tc->map_slo, dwlo, v.Vr, v.Vp))
         return HMC_ERR_CUDA;
     {
         // slice-major tiles: all sites in one tile up to 288; standalone
@@ -1331,7 +1446,7 @@ int tc_ctx_init(hmc_ctx* c) {
             return HMC_ERR_CUDA;
     }
     c->tc->ns_apply = pick_ns(v.Vr / tc::TM, v.Nt, c->num_sms);
-    if (c->params.tile_slices > 0 && c->params.operand_mode != 4)
+    if (c->params.tile_slices > 0 && c->params.operand_mode != 4 && c->params.operand_mode != 5)
         c->tc->ns_apply = c->params.tile_slices;
     {
         // pre-split B of standalone applications (rows padded by 64 zero rows)
@@ -1368,7 +1483,9 @@ int tc_ctx_init(hmc_ctx* c) {
                              (const void*)tc::k_cg<tc::kKindSmall>,
                              (const void*)tc::k_trajectory<tc::kKindSmall>,
                              (const void*)tc::k_cg<tc::kKindSlice>,
-                             (const void*)tc::k_trajectory<tc::kKindSlice>};
+                             (const void*)tc::k_trajectory<tc::kKindSlice>,
+                             (const void*)tc::k_cg<tc::kKindSplitK>,
+                             (const void*)tc::k_trajectory<tc::kKindSplitK>};
     for (const void* k : kernels)
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tc::kSmemBytes) != cudaSuccess)
@@ -1491,9 +1608,68 @@ static int small_cluster(const hmc_ctx* c) {
     return 0;
 }
 
+// Split-K shape (operand_mode 5): slices per n-group (tile_slices, else the
+// fewest n-groups of at most 64 slices, balanced) and CTAs per cluster
+// (inner_ctas, else the smallest of 6, 8, 4, 2 whose K range fits the
+// shared memory); false if the requested shape does not fit.
+static bool splitk_shape(const hmc_ctx* c, int* C_out, int* ns_out) {
+    const ChainView& v = c->view;
+    int ns = c->params.tile_slices;
+    if (ns <= 0) {
+        const int nng = (v.Nt + 63) / 64;
+        ns = (v.Nt + nng - 1) / nng;
+    }
+    if (ns < 1 || ns > 64) return false;
+    const int Nn = tc::sk_nn(ns);
+    const int KS = (v.V + 15) / 16;
+    auto fits = [&](int C) {
+        if (C < 2 || C > tc::kSkMaxCluster || C > KS) return false;
+        const int steps = (KS + C - 1) / C;
+        const int nch = tc::sk_chunks(steps);
+        const int own_slices = (std::min(ns, v.Nt) + C - 1) / C;
+        return nch <= tc::kSkMaxChunks &&
+               tc::sk_smem_total(nch, Nn, own_slices) <= tc::kOperandBytes;
+    };
+    int C = c->params.inner_ctas;
+    if (C > 0) {
+        if (!fits(C)) return false;
+    } else {
+        C = 0;
+        for (int cand : {6, 8, 4, 2})
+            if (fits(cand)) { C = cand; break; }
+        if (!C) return false;
+    }
+    *C_out = C;
+    *ns_out = ns;
+    return true;
+}
+
 static tc::PersistentArgs persistent_args(hmc_ctx* c, int grid, double tol, int max_iter) {
     tc::PersistentArgs pa;
     const ChainView& v = c->view;
+    pa.sk_C = 0;
+    if (c->params.operand_mode == 5) {
+        // split-K tiles with E' resident: nib x nng clusters of C CTAs form
+        // the inner team (0 CTAs if the shape does not fit)
+        int C = 0, ns = 0;
+        pa.mode = tc::kSplitK;
+        pa.inner = 0;
+        if (splitk_shape(c, &C, &ns)) {
+            pa.sk_C = C;
+            pa.ns_tile = ns;
+            pa.inner = (v.Vr / tc::TM) * ((v.Nt + ns - 1) / ns) * C;
+        }
+        pa.cluster = C;
+        pa.vec_resident = 0;
+        pa.res_b = 0;
+        pa.wide_W = 0;
+        pa.tol = tol;
+        pa.max_iter = max_iter;
+        pa.ru_delta = c->params.ru_delta;
+        pa.ru_every = c->params.ru_every;
+        (void)grid;
+        return pa;
+    }
     if (c->params.operand_mode == 3) {
         // CUDA-core cluster solver; grid is a multiple of the cluster size
         pa.mode = tc::kSmall;
@@ -1619,6 +1795,48 @@ static int launch_persistent(hmc_ctx* c, const void* fn, int grid, void** args,
                : HMC_ERR_CUDA;
 }
 
+// Split-K mode: a cooperative launch of thread-block clusters of sk_C CTAs,
+// as many clusters as can be resident at once (at least the inner team's;
+// team_ctas caps it), with the team-sum slots cleared first.
+static int launch_splitk(hmc_ctx* c, const void* fn, void** args, tc::PersistentArgs& pa,
+                         cudaStream_t s) {
+    if (pa.inner < 1 || pa.sk_C < 2) return HMC_ERR_UNSUPPORTED;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(tc::NTHR);
+    cfg.dynamicSmemBytes = tc::kSmemBytes;
+    cfg.stream = s;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)pa.sk_C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeCooperative;
+    at[1].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(pa.inner);
+    int nclu = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclu, fn, &cfg) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return HMC_ERR_UNSUPPORTED;
+    }
+    int grid = std::min(nclu * pa.sk_C, kMaxTeam / pa.sk_C * pa.sk_C);
+    if (c->params.team_ctas > 0)
+        grid = std::min(grid, std::max(c->params.team_ctas / pa.sk_C * pa.sk_C, pa.inner));
+    if (grid < pa.inner) return HMC_ERR_UNSUPPORTED;
+    cfg.gridDim = dim3(grid);
+    cfg.numAttrs = 2;
+    if (cudaMemsetAsync(c->view.gslots, 0, tc::kGatherSlots * sizeof(unsigned long long), s) !=
+        cudaSuccess)
+        return HMC_ERR_CUDA;
+    pa.cluster = pa.sk_C;
+    if (cudaLaunchKernelExC(&cfg, fn, args) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return HMC_ERR_UNSUPPORTED;
+    }
+    return HMC_OK;
+}
+
 // Small mode: the launch is a whole number of clusters.
 static int round_grid(const tc::PersistentArgs& pa, int grid) {
     if (pa.mode != tc::kSmall || pa.inner < 1) return grid;
@@ -1632,10 +1850,14 @@ int tc_cg(hmc_ctx* c, const double* phi, const double2* chi, double2* x, double 
     tc::PersistentArgs pa = persistent_args(c, grid, tol, max_iter);
     if (pa.mode == tc::kSmall && pa.inner < 1) return HMC_ERR_UNSUPPORTED;
     grid = round_grid(pa, grid);
+    ChainView v = c->view;
+    if (pa.mode == tc::kSplitK) {
+        void* args[] = {&c->tc->map_shi, &c->tc->map_slo, &v, &pa, &phi, &chi, &x};
+        return launch_splitk(c, (const void*)tc::k_cg<tc::kKindSplitK>, args, pa, s);
+    }
     const void* fn = pa.mode == tc::kSmall   ? (const void*)tc::k_cg<tc::kKindSmall>
                      : pa.mode == tc::kSlice ? (const void*)tc::k_cg<tc::kKindSlice>
                                              : (const void*)tc::k_cg<tc::kKindSite>;
-    ChainView v = c->view;
     const bool sl = pa.mode == tc::kSlice;
     void* args[] = {sl ? &c->tc->map_whi : &c->tc->map_hi, sl ? &c->tc->map_wlo : &c->tc->map_lo,
                     &v, &pa, &phi, &chi, &x};
@@ -1648,11 +1870,15 @@ int tc_trajectory(hmc_ctx* c, const TrajArgs& a, cudaStream_t s) {
     tc::PersistentArgs pa = persistent_args(c, grid, a.tol, a.max_iter);
     if (pa.mode == tc::kSmall && pa.inner < 1) return HMC_ERR_UNSUPPORTED;
     grid = round_grid(pa, grid);
+    ChainView v = c->view;
+    TrajArgs av = a;
+    if (pa.mode == tc::kSplitK) {
+        void* args[] = {&c->tc->map_shi, &c->tc->map_slo, &v, &pa, &av};
+        return launch_splitk(c, (const void*)tc::k_trajectory<tc::kKindSplitK>, args, pa, s);
+    }
     const void* fn = pa.mode == tc::kSmall   ? (const void*)tc::k_trajectory<tc::kKindSmall>
                      : pa.mode == tc::kSlice ? (const void*)tc::k_trajectory<tc::kKindSlice>
                                              : (const void*)tc::k_trajectory<tc::kKindSite>;
-    ChainView v = c->view;
-    TrajArgs av = a;
     const bool sl = pa.mode == tc::kSlice;
     void* args[] = {sl ? &c->tc->map_whi : &c->tc->map_hi, sl ? &c->tc->map_wlo : &c->tc->map_lo,
                     &v, &pa, &av};
@@ -1712,7 +1938,7 @@ int tc_batch_create(const hmc_params* p, int n, TcBatch** out) {
     std::vector<int> map_slot(n);
     int n_maps = 0;
     for (int i = 0; i < n && st == HMC_OK; ++i) {
-        if (p[i].precision != HMC_PREC_MIXED) st = HMC_ERR_UNSUPPORTED;
+        if (p[i].precision != HMC_PREC_MIXED || p[i].operand_mode == 5) st = HMC_ERR_UNSUPPORTED;
         hmc_ctx* c = nullptr;
         if (st == HMC_OK) st = hmc_ctx_create(&p[i], &c);
         if (st != HMC_OK) break;

@@ -40,8 +40,12 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint32_t bar, uint32_t parity)
         : "memory");
     return done;
 }
-// Wait for the phase of parity `parity` to complete; bounded.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status) {
+// Wait for the phase of parity `parity` to complete; bounded.  A wait for
+// this CTA's own copies in flight (stop_on_failure = false) keeps waiting,
+// within the limit, when the team has failed, so no copy lands after the
+// CTA has left.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status,
+                                          bool stop_on_failure = true) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t n = 1;; ++n) {
@@ -51,7 +55,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* st
                 set_status(status, HMC_ERR_TIMEOUT);
                 return false;
             }
-            if (*((volatile int*)status) != 0) return false;
+            if (stop_on_failure && *((volatile int*)status) != 0) return false;
         }
     }
 }

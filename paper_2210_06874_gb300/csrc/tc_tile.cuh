@@ -79,7 +79,10 @@ constexpr size_t kSmemBytes = kOperandBytes + sizeof(TileBars) + 1024;  // + ali
 //              small_cg.cuh lays out E^T and its vectors in the area
 //   slice:     slice-major tiles (tc_wide.cuh): a ring of U + E' stages
 //              from the start of the area, with its own barriers
-enum OperandMode : int { kStreaming = 0, kResident = 1, kSmall = 2, kSlice = 3 };
+//   splitk:    split-K tiles (tc_splitk.cuh): the CTA's rows x K range of
+//              E' resident (loaded once per launch), the stacked B of its
+//              chunks, and the staged partial accumulator
+enum OperandMode : int { kStreaming = 0, kResident = 1, kSmall = 2, kSlice = 3, kSplitK = 4 };
 
 __device__ __forceinline__ uint8_t* smem_base(uint8_t* dyn) {
     const uint32_t a = smem_u32(dyn);
@@ -301,6 +304,8 @@ struct TcState {
                        // depth depends on the tile width, so each stage's
                        // barrier phases are counted on their own)
     uint32_t wtile;    // slice-major tiles so far
+    uint32_t gseq;     // split-K: team sums posted so far (gather_sum_f)
+    int sk_loaded;     // split-K: this CTA's part of E' is resident
     int* status;
     __device__ __forceinline__ uint8_t* a_hi(int kc, int s) const {
         return base + (mode == kResident ? kc : s) * kAChunkBytes;
@@ -327,6 +332,8 @@ __device__ inline void tc_setup(TcState& st, uint8_t* dyn, int* status) {
     st.nres = 0;
     for (int s = 0; s < 4; ++s) st.wuse[s] = 0;
     st.wtile = 0;
+    st.gseq = 0;
+    st.sk_loaded = 0;
     st.status = status;
     TileBars& b = *st.bars;
     if (threadIdx.x == 0) {

@@ -5,8 +5,8 @@ For one chain it times short mixed CG solves with a fixed iteration count
 not depend on the residual) for candidate shapes -- CTAs of the persistent
 launch (team_ctas), CTAs of the FP32 inner loop (inner_ctas), time slices per
 tensor-core tile (tile_slices), streamed or resident E, site-major or
-slice-major tiles, CUDA-core cluster mode (operand_mode) -- and keeps the
-fastest.  Timing uses CUDA
+slice-major tiles, CUDA-core cluster mode, split-K tiles with E resident
+(operand_mode) -- and keeps the fastest.  Timing uses CUDA
 events on the current stream around calls through the C ABI; results are
 cached per (L, Nt, team constraint) for the process.
 """
@@ -85,6 +85,12 @@ def candidates(params, num_sms, single_cta=False):
     else:
         for inner in (1, 2, 4, 8):
             out.append((max(inner, min(f64_tiles, num_sms)), inner, 0, 4))
+        if V >= 128:
+            # split-K tiles with E resident, clusters of C CTAs (the launch
+            # takes as many clusters as fit; shapes the library refuses are
+            # skipped)
+            for C in (2, 4, 6, 8):
+                out.append((0, C, 0, 5))
     return sorted(set(out))
 
 

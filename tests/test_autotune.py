@@ -9,12 +9,18 @@ def test_candidates_cover_one_cta_and_tile_teams():
     assert (12, 1, 16, 2) in c                   # resident E, one site block
     assert all(ns in (8, 16, 32) for _, _, ns, m in c if m != 4)
     assert (12, 1, 0, 4) in c and (12, 8, 0, 4) in c   # slice-major, slices chosen by the library
-    assert all(inner <= team <= 148 for team, inner, _, _ in c)
+    assert all(inner <= team <= 148 for team, inner, _, m in c if m != 5)
+    assert not any(m == 5 for *_, m in c)            # split-K tiles: V >= 128 only
     single = autotune.candidates(p, num_sms=148, single_cta=True)
     assert single == [(1, 1, 0, 4), (1, 1, 8, 1), (1, 1, 8, 2), (1, 1, 16, 1), (1, 1, 16, 2),
                       (1, 1, 32, 1)]
     big = autotune.candidates(hmc.Params(L=24, Nt=96, beta=12.0), num_sms=148)
-    assert all(mode in (1, 4) for *_, mode in big)    # E rows too large to stay resident
+    assert all(mode in (1, 4, 5) for *_, mode in big)  # E rows too large to stay resident
+    # split-K tiles: clusters of 2..8 CTAs, the launch size left to the library
+    assert [s for s in big if s[3] == 5] == [(0, 2, 0, 5), (0, 4, 0, 5), (0, 6, 0, 5),
+                                             (0, 8, 0, 5)]
+    assert (0, 6, 0, 5) not in autotune.candidates(hmc.Params(L=6, Nt=32, beta=4.0),
+                                                   num_sms=148, single_cta=True)
 
 
 def test_pick_fastest_then_fewest_ctas():

@@ -52,8 +52,11 @@ def parse():
                     help="trajectory mode: steps per trajectory (default: the workload's)")
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "mixed"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="trajectory", choices=["trajectory", "apply", "brs"],
-                    help="trajectory: HMC trajectories/s; apply: M-applications/s")
+    ap.add_argument("--mode", default="trajectory", choices=["trajectory", "apply", "brs", "cg"],
+                    help="trajectory: HMC trajectories/s; apply: M-applications/s; cg: "
+                         "M-applications/s inside the mixed CG (us per FP32 iteration)")
+    ap.add_argument("--cg-iters", type=int, default=400,
+                    help="cg mode: FP32 iterations of the longer timed solve")
     ap.add_argument("--brs-L", type=int, default=102, help="brs mode: lattice size")
     ap.add_argument("--brs-Nt", type=int, default=256, help="brs mode: time slices")
     ap.add_argument("--applies", type=int, default=20,
@@ -471,7 +474,7 @@ def run_reference(args):
               flush=True)
         return
     batch = name.startswith("batch")
-    apply = args.mode == "apply" and not batch
+    apply = args.mode in ("apply", "cg") and not batch
     by_iters = None
     if not batch and not apply and 2 * synth.WORKLOADS[name]["L"] ** 2 >= 288:
         by_iters = reference_iteration_setup(name, args)
@@ -480,6 +483,17 @@ def run_reference(args):
         t0 = time.perf_counter()
         if batch:
             r = cpu_oracle_batch_rate(args.chains, sample_s)
+        elif apply and args.mode == "cg":
+            w = synth.WORKLOADS[name]
+            V, Nt = 2 * w["L"] ** 2, w["Nt"]
+            phi0 = synth.gaussian_field(w["seed"], Nt, V, w["beta"] / Nt * w["U"], scale=0.3)
+            chi0 = synth.complex_gaussian(w["seed"] + 1, Nt, V)
+            per, it, dt = cpu_oracle_cg_iter_time(name, phi0, chi0, sample_s)
+            r = {"value": 2.0 / per, "unit": "M-applications/s", "cores": os.cpu_count(),
+                 "kind": "oracle",
+                 "sample": "%d FP64 CG iterations of the oracle on %s (%.1f s), two "
+                           "applications each; NumPy FP64, BLAS threads as configured"
+                           % (it, name, dt)}
         elif apply:
             r = cpu_oracle_apply_rate(name, sample_s)
         elif by_iters:
@@ -504,7 +518,7 @@ def run_reference(args):
         w = synth.WORKLOADS[name]
         config = {"workload": name, "precision": "fp64 (oracle)", "L": w["L"], "Nt": w["Nt"]}
         if apply:
-            config["mode"] = "apply"
+            config["mode"] = args.mode
         else:
             config.update(n_md=args.n_md or w["n_md"], integrator=args.integrator)
     line = {
@@ -853,6 +867,100 @@ def run_apply(args):
         print(json.dumps(line), flush=True)
 
 
+def run_cg(args):
+    """Microseconds per FP32 iteration of the mixed CG (two applications, two
+    team sums and the vector updates) on the workload's lattice, in the
+    autotuned (or --operand-mode) launch shape: the difference of two solves
+    of cg_iters and cg_iters / 4 iterations (tolerance never met, reliable
+    updates off), so the FP64 residual at the end of a solve cancels.
+    value = M-applications/s inside the CG; the FP64 path's seconds per CG
+    iteration on the same problem beside it."""
+    import torch
+    from paper_2210_06874_gb300 import build_lib, hmc, synth
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    build_lib.build()
+    name = args.workload
+    w, params, _ = workload_params(name, "mixed")
+    if args.operand_mode is not None:
+        params.operand_mode = args.operand_mode
+    elif not args.no_tune:
+        from paper_2210_06874_gb300 import autotune
+        params = autotune.tune(params)
+    params.ru_delta = 1e-30
+    params.ru_every = 1 << 30
+    ctx = hmc.Context(params)
+    V, Nt = params.V, params.Nt
+    dev = torch.device("cuda", local_rank)
+    phi = torch.from_numpy(synth.gaussian_field(w["seed"], Nt, V, w["beta"] / Nt * w["U"],
+                                                scale=0.3)).to(dev)
+    chi = torch.from_numpy(synth.complex_gaussian(w["seed"] + 1, Nt, V)).to(dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush_acc = torch.empty((), dtype=torch.float32, device=dev)
+    n_long, n_short = args.cg_iters, max(1, args.cg_iters // 4)
+
+    def solve_ms(prec, iters):
+        flush_l2(flush, flush_acc)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        _, st = ctx.cg_solve(phi, chi, tol=1e-300, max_iter=iters, prec=prec,
+                             allow_not_converged=True)
+        e.record(stream)
+        e.synchronize()
+        assert st.iterations == iters, (st.iterations, iters)
+        return s.elapsed_time(e)
+
+    for _ in range(max(1, args.warmup)):
+        solve_ms(hmc.PREC_MIXED, n_short)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    per_it = []
+    for _ in range(args.steps):
+        per_it.append((solve_ms(hmc.PREC_MIXED, n_long) - solve_ms(hmc.PREC_MIXED, n_short)) /
+                      (n_long - n_short))
+    clk = clocks.stop()
+    ms_it = statistics.median(per_it)
+    n64 = max(8, n_long // 20)
+    ms64 = (solve_ms(hmc.PREC_FP64, 2 * n64) - solve_ms(hmc.PREC_FP64, n64)) / n64
+    peaks, kind = load_peaks()
+    flop = 2 * flops_per_apply(V, Nt)
+    byts = 2 * apply_bytes(V, Nt, "mixed")
+    peak = peaks.get("bf16_tflops", FALLBACK["bf16_tflops"])
+    hbm_peak = peaks.get("hbm_gbs", FALLBACK["hbm_gbs"])
+    achieved = flop / (ms_it * 1e-3) / 1e12
+    traffic_it, traffic_src = committed_traffic(name, "per-cg-iteration")
+    line = {"metric": METRIC, "value": 2e3 / ms_it, "unit": "M-applications/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.mean(per_it) * (n_long - n_short),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16-split/f32", "data": "synthetic",
+            "config": {"workload": name, "mode": "cg", "V": V, "Nt": Nt,
+                       "iterations": [n_short, n_long],
+                       "launch_shape": {"team_ctas": params.team_ctas,
+                                        "inner_ctas": params.inner_ctas,
+                                        "tile_slices": params.tile_slices,
+                                        "operand_mode": params.operand_mode},
+                       "field": "phi ~ 0.3 N(0, delta U), chi complex Gaussian",
+                       "l2": "flushed (256 MB write + read sweep) before every solve"},
+            "us_per_cg_iteration": 1e3 * ms_it,
+            "fp64_us_per_cg_iteration": 1e3 * ms64,
+            "gpu_launches": 2 * args.steps,
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": (traffic_it * 1.0) if traffic_it is not None else None,
+                         "traffic_source": traffic_src,
+                         "flop_per_iteration": flop,
+                         "peak_source": "%s bf16 dense burst (fp16 has the same rate)" % kind,
+                         "hbm": {"achieved_gbs": byts / (ms_it * 1e-3) / 1e9,
+                                 "peak_gbs": hbm_peak, "algorithmic_bytes": byts,
+                                 "frac": byts / (ms_it * 1e-3) / 1e9 / hbm_peak}},
+            "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_batch(args):
     """Batched workload: many chains of uneven size, one persistent launch per
     trajectory of every chain (hmc_batch_trajectory); value = aggregate
@@ -1109,6 +1217,9 @@ def main():
         return
     if args.mode == "apply" and args.impl == "ours":
         run_apply(args)
+        return
+    if args.mode == "cg" and args.impl == "ours":
+        run_cg(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -1825,7 +1826,12 @@ static int launch_splitk(hmc_ctx* c, const void* fn, void** args, tc::Persistent
         grid = std::min(grid, std::max(c->params.team_ctas / pa.sk_C * pa.sk_C, pa.inner));
     if (grid < pa.inner) return HMC_ERR_UNSUPPORTED;
     cfg.gridDim = dim3(grid);
-    cfg.numAttrs = 2;
+    // HMC_PROFILE_NONCOOPERATIVE=1: the same launch without the cooperative
+    // attribute, for profilers that refuse cooperative cluster launches.  The
+    // grid is the clusters that can be resident at once, so in practice every
+    // CTA runs; were one not resident, the bounded team waits would end the
+    // launch with HMC_ERR_TIMEOUT.
+    cfg.numAttrs = getenv("HMC_PROFILE_NONCOOPERATIVE") ? 1 : 2;
     if (cudaMemsetAsync(c->view.gslots, 0, tc::kGatherSlots * sizeof(unsigned long long), s) !=
         cudaSuccess)
         return HMC_ERR_CUDA;

@@ -15,6 +15,10 @@ operators  E = exp(delta*kappa*h); the fermion matrix M[phi] and M^dagger[phi]
 hmc        CG on M M^dagger, action Eq. (2.1), force, leapfrog, Metropolis (§2)
 philox     Philox4x32-10 counter-based generator (Salmon et al., SC'11) and
            the Box-Muller normals drawn from it
+hasenbusch mass preconditioning (Hasenbusch 2001) with a two-level nested
+           leapfrog (Sexton and Weingarten 1992): heavy operator, the two
+           pseudofermions, their forces, the nested schedule, a trajectory
+observables zero-momentum single-particle correlator from one M^{-1} source
 
 Conventions (readings of the paper where it leaves a choice):
   * field phi is the product delta*phi_paper, so phases are exp(+i phi) and the

@@ -28,6 +28,7 @@ MASK32 = np.uint64(0xFFFFFFFF)
 STREAM_MOMENTUM = 0
 STREAM_PSEUDOFERMION = 1
 STREAM_METROPOLIS = 2
+STREAM_HEAVY = 3          # second pseudofermion of mass preconditioning
 
 
 def philox4x32_10(c0, c1, c2, c3, k0, k1):

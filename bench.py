@@ -51,6 +51,11 @@ def parse():
     ap.add_argument("--n-md", type=int, default=None,
                     help="trajectory mode: steps per trajectory (default: the workload's)")
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "mixed"])
+    ap.add_argument("--hb-inner", type=int, default=0,
+                    help="trajectory mode, FP64: mass preconditioning with this many inner "
+                         "leapfrog steps per outer step (0: off; n_md counts outer steps)")
+    ap.add_argument("--hb-gamma", type=float, default=0.5,
+                    help="hop factor g of the heavy operator M_g = 1 - g S E D")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="trajectory", choices=["trajectory", "apply", "brs", "cg"],
                     help="trajectory: HMC trajectories/s; apply: M-applications/s; cg: "
@@ -258,9 +263,11 @@ def measure_dgemm_tflops(torch):
     return 2.0 * n ** 3 / (best * 1e-3) / 1e12
 
 
-def cpu_oracle_rate(name, prec, sample_s, phi_np=None, integrator="leapfrog", n_md=None):
+def cpu_oracle_rate(name, prec, sample_s, phi_np=None, integrator="leapfrog", n_md=None,
+                    hb=None):
     """Time the CPU oracle (as it stands) on trajectories of the same workload
-    (and integrator) until about sample_s seconds of work are done."""
+    (and integrator; hb = (g, inner steps): mass preconditioning) until
+    about sample_s seconds of work are done."""
     import numpy as np
     from oracle import hmc as ohmc, lattice, operators as ops
     from paper_2210_06874_gb300 import synth
@@ -273,9 +280,16 @@ def cpu_oracle_rate(name, prec, sample_s, phi_np=None, integrator="leapfrog", n_
     iters = 0
     n_md = n_md or w["n_md"]
     while True:
-        out = ohmc.trajectory(E, phi, delta, w["U"], w["traj_length"] / n_md, n_md,
-                              w["seed"], 10_000 + n, 0, tol=w["cg_tol"], max_iter=200000,
-                              integrator=integrator)
+        if hb:
+            from oracle import hasenbusch as ohb
+            out = ohb.trajectory(E, phi, delta, w["U"], hb[0], w["traj_length"] / n_md, n_md,
+                                 hb[1], w["seed"], 10_000 + n, 0, tol=w["cg_tol"],
+                                 max_iter=200000)
+            out["cg_iters"] = out["cg_iters_inner"] + out["cg_iters_outer"]
+        else:
+            out = ohmc.trajectory(E, phi, delta, w["U"], w["traj_length"] / n_md, n_md,
+                                  w["seed"], 10_000 + n, 0, tol=w["cg_tol"], max_iter=200000,
+                                  integrator=integrator)
         phi = out["phi"]
         iters += out["cg_iters"]
         n += 1
@@ -585,6 +599,8 @@ def run_ours(args):
     if args.n_md is not None:
         params.n_md = args.n_md
     params.integrator = 1 if args.integrator == "omelyan" else 0
+    if args.hb_inner > 0:
+        params.hb_inner, params.hb_gamma = args.hb_inner, args.hb_gamma
     tuned = None
     if prec == "mixed" and args.operand_mode is not None:
         params.operand_mode = args.operand_mode
@@ -716,6 +732,7 @@ def run_ours(args):
                    "launch_shape": tuned or "automatic"},
         "m_applications_per_s": world * n_app / (ms_per_step * 1e-3),
         "cg_iterations_per_traj": mean_iters,
+        "cg_solves_per_traj": statistics.mean(o.cg_solves for o in outs),
         "cg_iterations_per_s": world * mean_iters / (ms_per_step * 1e-3),
         "acceptance": statistics.mean(o.accept for o in outs),
         "mean_abs_dH": statistics.mean(abs(o.dH) for o in outs),
@@ -727,6 +744,12 @@ def run_ours(args):
         "clocks": clk,
         "wall_s_timed_region": wall,
     }
+    if args.hb_inner > 0:
+        line["config"]["mass_preconditioning"] = {"hb_gamma": args.hb_gamma,
+                                                  "hb_inner": args.hb_inner}
+        line["cg_solves_outer_per_traj"] = statistics.mean(o.cg_solves_outer for o in outs)
+        line["cg_iterations_outer_per_traj"] = statistics.mean(o.cg_iterations_outer
+                                                               for o in outs)
     if cmp:
         t64 = cmp["fp64"]["ms"] * 1e-3 * n_solves
         cmp["fp64_trajectories_per_s_est"] = 1.0 / t64
@@ -748,12 +771,14 @@ def run_ours(args):
                 name, phi_np, chi_np, min(args.cpu_sample_s, 10.0), cmp["fp64"]["iterations"],
                 n_solves, single_thread=True)
         else:
+            hbk = (args.hb_gamma, args.hb_inner) if args.hb_inner > 0 else None
             line["cpu_baseline"] = cpu_oracle_rate(name, prec, args.cpu_sample_s,
                                                    phi_np=phi_np, integrator=args.integrator,
-                                                   n_md=params.n_md)
-            line["cpu_baseline"]["single_thread"] = cpu_oracle_rate_single_thread(
-                name, prec, min(args.cpu_sample_s, 10.0), phi_np=phi_np,
-                integrator=args.integrator, n_md=params.n_md)
+                                                   n_md=params.n_md, hb=hbk)
+            if not hbk:
+                line["cpu_baseline"]["single_thread"] = cpu_oracle_rate_single_thread(
+                    name, prec, min(args.cpu_sample_s, 10.0), phi_np=phi_np,
+                    integrator=args.integrator, n_md=params.n_md)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

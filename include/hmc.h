@@ -140,6 +140,19 @@ typedef struct hmc_params {
                             residual check; two checks in a row that do not
                             halve the true residual switch the rest of the
                             solve to FP64 CG iterations */
+    double hb_gamma;     /* mass preconditioning (Hasenbusch, Phys. Lett. B 519
+                            (2001) 177): hop factor g in [0, 1) of the heavy
+                            operator M_g = 1 - g S E D (used when hb_inner > 0) */
+    int hb_inner;        /* 0: one pseudofermion (the plain HMC of §2); 1..64:
+                            hmc_trajectory uses two pseudofermions, chi_1 for
+                            det(M_g M_g^dag) and chi_2 for det(M M^dag) /
+                            det(M_g M_g^dag), on a two-level leapfrog (Sexton
+                            and Weingarten, Nucl. Phys. B 380 (1992) 665): n_md
+                            outer steps for the ratio force, hb_inner inner
+                            steps per outer step for the bosonic and heavy
+                            forces.  The same target density.  FP64 precision
+                            only (HMC_ERR_UNSUPPORTED otherwise); integrator
+                            must be 0 */
 } hmc_params;
 
 typedef struct hmc_cg_stats {
@@ -161,6 +174,9 @@ typedef struct hmc_traj_out {
     double max_true_residual;
     int status;
     int fp64_iterations;     /* MIXED: FP64 CG iterations of stalled solves */
+    int cg_iterations_outer; /* mass preconditioning: the ratio solves' share of
+                                cg_iterations (0 otherwise) */
+    int cg_solves_outer;     /* ... and of cg_solves */
 } hmc_traj_out;
 
 typedef struct hmc_ctx hmc_ctx;

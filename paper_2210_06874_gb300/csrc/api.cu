@@ -144,6 +144,9 @@ static int valid_params(const hmc_params* p) {
     if (p->cluster_mode < 0 || p->cluster_mode > 2) return 0;
     if (p->integrator < 0 || p->integrator > 1) return 0;
     if (p->ru_every < 0) return 0;
+    if (p->hb_inner < 0 || p->hb_inner > 64) return 0;
+    if (p->hb_inner > 0 && (!(p->hb_gamma >= 0.0 && p->hb_gamma < 1.0) || p->integrator != 0))
+        return 0;
     // |delta mu| <= 5: the scaled E keeps its FP16 split in range
     if (!std::isfinite(p->mu) || std::fabs(p->mu * p->beta / p->Nt) > 5.0) return 0;
     if (p->operand_mode == 4 || p->operand_mode == 5) {
@@ -216,6 +219,11 @@ int hmc_ctx_create(const hmc_params* p, hmc_ctx** out) {
     v.chi = (double2*)ctx_alloc(c, N * sizeof(double2), &ok);
     v.rho = (double2*)ctx_alloc(c, N * sizeof(double2), &ok);
     v.xh = (double2*)ctx_alloc(c, N * sizeof(double2), &ok);
+    if (p->hb_inner > 0) {
+        v.chi2 = (double2*)ctx_alloc(c, N * sizeof(double2), &ok);
+        v.phi2 = (double2*)ctx_alloc(c, N * sizeof(double2), &ok);
+        v.x2 = (double2*)ctx_alloc(c, N * sizeof(double2), &ok);
+    }
     v.pi = (double*)ctx_alloc(c, N * sizeof(double), &ok);
     v.phi_old = (double*)ctx_alloc(c, N * sizeof(double), &ok);
     v.bar = (unsigned*)ctx_alloc(c, 8 * sizeof(unsigned), &ok);
@@ -359,6 +367,9 @@ int hmc_trajectory(hmc_ctx* c, double* phi, uint64_t seed, uint64_t traj_index, 
     a.max_iter = c->params.cg_max_iter;
     a.ru_delta = c->params.ru_delta;
     a.integrator = c->params.integrator;
+    a.hb_gamma = c->params.hb_gamma;
+    a.hb_inner = c->params.hb_inner;
+    if (a.hb_inner > 0 && c->params.precision != HMC_PREC_FP64) return HMC_ERR_UNSUPPORTED;
     int st;
     if (c->params.precision == HMC_PREC_FP64)
         st = launch_trajectory_f64(c->view, c->num_sms, a, s);
@@ -381,6 +392,8 @@ int hmc_trajectory(hmc_ctx* c, double* phi, uint64_t seed, uint64_t traj_index, 
     out->reliable_updates = (int)v[kTrajRU];
     out->max_true_residual = v[kTrajMaxRes];
     out->fp64_iterations = (int)v[kTrajFp64Iters];
+    out->cg_iterations_outer = (int)v[kTrajItersOuter];
+    out->cg_solves_outer = (int)v[kTrajSolvesOuter];
     out->status = dev != 0 ? dev : (int)v[kTrajStatus];
     return out->status;
 }

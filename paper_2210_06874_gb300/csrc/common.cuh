@@ -42,7 +42,8 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
     return c;
 }
 
-enum : uint32_t { kStreamMomentum = 0, kStreamNoise = 1, kStreamMetropolis = 2 };
+enum : uint32_t { kStreamMomentum = 0, kStreamNoise = 1, kStreamMetropolis = 2,
+                  kStreamHeavy = 3 };   // 3: the heavy pseudofermion of mass preconditioning
 
 // Counter (element, stream, trajectory mod 2^32, chain), key = seed halves.
 __device__ __forceinline__ uint4 philox_draw(uint64_t seed, uint32_t stream, uint64_t traj,

@@ -28,6 +28,8 @@ struct ChainView {
     double2 *cis;               // exp(i phi)
     double2 *x, *r, *p, *q, *chi, *rho;
     double2 *xh;                // solution history for the mixed trajectory's guesses
+    double2 *chi2, *phi2, *x2;  // mass preconditioning: second pseudofermion, M_g chi2,
+                                // and its solve (allocated when hb_inner > 0)
     double *pi, *phi_old;       // double [Nt][V]
     // FP32 workspaces for the mixed path, float2 [Nt][V] each
     float2 *cis_f, *r_f, *p_f, *p2_f, *q_f, *x_f;
@@ -58,7 +60,7 @@ struct hmc_ctx {
     int num_sms;
     hmc::ChainView view;
     // owned device allocations (freed by hmc_ctx_destroy)
-    void* allocs[32];
+    void* allocs[64];
     int n_allocs;
     double* scalars_host;       // pinned, mirrors view.scalars
 };

@@ -185,6 +185,160 @@ __global__ void __launch_bounds__(NTHR) k_trajectory(ChainView c, TrajArgs a) {
     }
 }
 
+// One HMC trajectory with mass preconditioning (Hasenbusch 2001) and the
+// two-level nested leapfrog (Sexton and Weingarten 1992), all in FP64.
+// Heavy operator M_g = 1 - g S E D (the contraction scaled by g); two
+// pseudofermions chi_1 = M_g rho_1 (rho_1 from stream 3) and
+// chi_2 = M_g^{-1} M rho_2 = M_g^dag (M_g M_g^dag)^{-1} M rho_2 (rho_2 from
+// the plain noise stream), H = S_B + chi_1^dag (M_g M_g^dag)^{-1} chi_1
+// + phi_2^dag (M M^dag)^{-1} phi_2 + pi^2/2 with phi_2 = M_g chi_2.
+// Outer level (n_md steps of eps): the ratio force
+//     F_2 = 2 Im(x_2 conj(M^dag x_2)) - 2 Im(conj(M_g^dag x_2 - x_2) chi_2);
+// inner level (hb_inner steps of eps / hb_inner inside each outer step):
+//     F_B + F_1 = phi / (delta U) + 2 Im(x_1 conj(M_g^dag x_1)).
+// Consecutive inner kicks are merged.  Every solve starts from zero.
+// Scalars as k_trajectory, plus the outer level's CG iterations and solves.
+__global__ void __launch_bounds__(NTHR) k_trajectory_hb(ChainView c, TrajArgs a) {
+    __shared__ Smem sm;
+    Team tm = make_team(c);
+    double* phi = a.phi;
+    const double inv_dU = 1.0 / (c.delta * c.U);
+    const double rsqrt2 = 0.70710678118654752440;
+    const double gm1 = a.hb_gamma - 1.0;
+    // 1. heat bath: momenta, the two noise vectors, start energy
+    double h0[3] = {0.0, 0.0, 0.0};
+    HMC_TEAM_ELEMS(e, c, tm) {
+        const double2 zp = normal_pair(philox_draw(a.seed, kStreamMomentum, a.traj, a.chain, e));
+        const double2 z2 = normal_pair(philox_draw(a.seed, kStreamNoise, a.traj, a.chain, e));
+        const double2 z1 = normal_pair(philox_draw(a.seed, kStreamHeavy, a.traj, a.chain, e));
+        const double ph = phi[e];
+        c.pi[e] = zp.x;
+        const double2 r1 = make_double2(z1.x * rsqrt2, z1.y * rsqrt2);
+        const double2 r2 = make_double2(z2.x * rsqrt2, z2.y * rsqrt2);
+        c.rho[e] = r1;
+        c.xh[e] = r2;
+        c.phi_old[e] = ph;
+        double s, co;
+        sincos(ph, &s, &co);
+        c.cis[e] = make_double2(co, s);
+        h0[0] += ph * ph;
+        h0[1] += r1.x * r1.x + r1.y * r1.y + r2.x * r2.x + r2.y * r2.y;
+        h0[2] += zp.x * zp.x;
+    }
+    if (!team_sum<3>(tm, h0)) return;
+    // S_1 = rho_1^dag rho_1 and S_2 = rho_2^dag rho_2 at the start field
+    const double H0 = 0.5 * h0[0] * inv_dU + h0[1] + 0.5 * h0[2];
+    // 2. chi_1 = M_g rho_1; chi_2 = M_g^dag (M_g M_g^dag)^{-1} M rho_2
+    EpiArgs eg = {};
+    eg.hop_m1 = gm1;
+    EpiArgs e1 = {};
+    apply_team<false, EPI_STORE>(c, tm, c.rho, c.chi, eg, sm);
+    apply_team<false, EPI_STORE>(c, tm, c.xh, c.phi2, e1, sm);
+    if (!team_barrier(tm)) return;
+    int iters_in = 0, iters_out = 0, solves_in = 0, solves_out = 0, status = HMC_OK;
+    double max_res = 0.0;
+    CgResult res;
+    if (!cg_solve(c, tm, c.phi2, c.x2, a.tol, a.max_iter, res, sm, false, gm1)) return;
+    iters_in += res.iterations;
+    ++solves_in;
+    max_res = fmax(max_res, res.true_res);
+    if (res.status != HMC_OK) status = res.status;
+    apply_team<true, EPI_STORE>(c, tm, c.x2, c.chi2, eg, sm);
+    if (!team_barrier(tm)) return;
+    // 3. nested leapfrog
+    const double ed = a.eps * c.delta;
+    const double h = 1.0 / a.hb_inner;
+    auto drift = [&](double cf) {
+        HMC_TEAM_ELEMS(e, c, tm) {
+            const double ph = fma(cf * ed, c.pi[e], phi[e]);
+            phi[e] = ph;
+            double s, co;
+            sincos(ph, &s, &co);
+            c.cis[e] = make_double2(co, s);
+        }
+        return team_barrier(tm);
+    };
+    auto kick_inner = [&](double cf) {
+        CgResult r;
+        if (!cg_solve(c, tm, c.chi, c.x, a.tol, a.max_iter, r, sm, false, gm1)) return false;
+        iters_in += r.iterations;
+        ++solves_in;
+        max_res = fmax(max_res, r.true_res);
+        if (r.status != HMC_OK && status == HMC_OK) status = r.status;
+        EpiArgs ef = {};
+        ef.hop_m1 = gm1;
+        ef.phi = phi;
+        ef.pi = c.pi;
+        ef.inv_dU = inv_dU;
+        ef.kick = cf * ed;
+        apply_team<true, EPI_FORCE>(c, tm, c.x, nullptr, ef, sm);
+        return team_barrier(tm);
+    };
+    auto kick_outer = [&](double cf) {
+        apply_team<false, EPI_STORE>(c, tm, c.chi2, c.phi2, eg, sm);   // phi_2 = M_g chi_2
+        if (!team_barrier(tm)) return false;
+        CgResult r;
+        if (!cg_solve(c, tm, c.phi2, c.x2, a.tol, a.max_iter, r, sm)) return false;
+        iters_out += r.iterations;
+        ++solves_out;
+        max_res = fmax(max_res, r.true_res);
+        if (r.status != HMC_OK && status == HMC_OK) status = r.status;
+        EpiArgs ef = {};
+        ef.phi = phi;
+        ef.pi = c.pi;
+        ef.inv_dU = 0.0;              // the bosonic force sits on the inner level
+        ef.kick = cf * ed;
+        apply_team<true, EPI_FORCE>(c, tm, c.x2, nullptr, ef, sm);
+        if (!team_barrier(tm)) return false;
+        ef.hop_m1 = gm1;
+        ef.chi = c.chi2;
+        apply_team<true, EPI_RATIO>(c, tm, c.x2, nullptr, ef, sm);
+        return team_barrier(tm);
+    };
+    if (!kick_outer(0.5)) return;
+    for (int k = 0; k < a.n_md; ++k) {
+        for (int m = 0; m < a.hb_inner; ++m) {
+            if (!kick_inner(m == 0 ? 0.5 * h : h)) return;
+            if (!drift(h)) return;
+        }
+        if (!kick_inner(0.5 * h)) return;
+        if (!kick_outer(k + 1 < a.n_md ? 1.0 : 0.5)) return;
+    }
+    // 4. end energy (the last kick of each level was at the final field) and
+    // Metropolis
+    double h1[4] = {0.0, 0.0, 0.0, 0.0};
+    HMC_TEAM_ELEMS(e, c, tm) {
+        const double ph = phi[e], pv = c.pi[e];
+        const double2 c1 = c.chi[e], x1 = c.x[e], p2 = c.phi2[e], x2 = c.x2[e];
+        h1[0] += ph * ph;
+        h1[1] += c1.x * x1.x + c1.y * x1.y;
+        h1[2] += p2.x * x2.x + p2.y * x2.y;
+        h1[3] += pv * pv;
+    }
+    if (!team_sum<4>(tm, h1)) return;
+    const double H1 = 0.5 * h1[0] * inv_dU + h1[1] + h1[2] + 0.5 * h1[3];
+    const double dH = H1 - H0;
+    const double u = uniform_pair(philox_draw(a.seed, kStreamMetropolis, a.traj, a.chain, 0)).x;
+    const bool accept = u < exp(-dH);
+    if (!accept) {
+        HMC_TEAM_ELEMS(e, c, tm) phi[e] = c.phi_old[e];
+    }
+    if (tm.rank == 0 && threadIdx.x == 0) {
+        c.scalars[kTrajDH] = dH;
+        c.scalars[kTrajH0] = H0;
+        c.scalars[kTrajH1] = H1;
+        c.scalars[kTrajU] = u;
+        c.scalars[kTrajAccept] = accept ? 1.0 : 0.0;
+        c.scalars[kTrajIters] = iters_in + iters_out;
+        c.scalars[kTrajSolves] = solves_in + solves_out;
+        c.scalars[kTrajRU] = 0;
+        c.scalars[kTrajMaxRes] = max_res;
+        c.scalars[kTrajStatus] = status;
+        c.scalars[kTrajItersOuter] = iters_out;
+        c.scalars[kTrajSolvesOuter] = solves_out;
+    }
+}
+
 }  // namespace f64
 
 // ------------------------------------------------------------ launchers
@@ -252,14 +406,15 @@ int launch_cg_f64(const ChainView& c, int num_sms, const double* phi, const doub
 
 int launch_trajectory_f64(const ChainView& c, int num_sms, const TrajArgs& a, cudaStream_t s) {
     const int nt = ((c.V + f64::TI - 1) / f64::TI) * ((c.Nt + f64::TT - 1) / f64::TT);
-    const int grid = persistent_grid((const void*)f64::k_trajectory, f64::NTHR, num_sms, nt);
+    const void* fn = a.hb_inner > 0 ? (const void*)f64::k_trajectory_hb
+                                    : (const void*)f64::k_trajectory;
+    if (a.hb_inner > 0 && (!c.chi2 || !c.phi2 || !c.x2)) return HMC_ERR_BAD_ARG;
+    const int grid = persistent_grid(fn, f64::NTHR, num_sms, nt);
     if (grid < 1) return HMC_ERR_CUDA;
     ChainView cv = c;
     TrajArgs av = a;
     void* args[] = {&cv, &av};
-    return launch_coop((const void*)f64::k_trajectory, grid, f64::NTHR, args, s) == cudaSuccess
-               ? HMC_OK
-               : HMC_ERR_CUDA;
+    return launch_coop(fn, grid, f64::NTHR, args, s) == cudaSuccess ? HMC_OK : HMC_ERR_CUDA;
 }
 
 }  // namespace hmc

@@ -33,6 +33,8 @@ enum Epi : int {
     EPI_RESIDUAL = 2,    // r = chi - M(in); partial |r|^2
     EPI_FORCE = 3,       // M^dag x -> y; F = phi/(dU) + 2 Im(x conj y);
                          //   store F if F != null; pi -= kick * F if pi != null
+    EPI_RATIO = 4,       // M_g^dag x -> y; pi -= kick * (-2 Im(conj(y - x) chi)):
+                         //   the M_g part of the ratio force of mass preconditioning
 };
 
 struct EpiArgs {
@@ -46,6 +48,8 @@ struct EpiArgs {
     double* pi;
     double kick;
     double inv_dU;   // 1 / (delta U)
+    double hop_m1;   // hop - 1: the contraction is scaled by hop (M_g of mass
+                     // preconditioning uses hop = g; 0 here is the plain M)
 };
 
 __device__ __forceinline__ int num_tiles(const ChainView& c) {
@@ -99,7 +103,8 @@ __device__ double apply_tile(const ChainView& c, int tile, const double2* __rest
     const int i = i0 + ii, t = t0 + tt;
     if (i >= V || t >= Nt) return 0.0;
     const size_t o = (size_t)t * V + i;
-    double2 w = make_double2(ar, ai);
+    const double hop = 1.0 + ea.hop_m1;
+    double2 w = make_double2(ar * hop, ai * hop);
     double sgn;
     if (DAG) {
         sgn = (t == Nt - 1) ? -1.0 : 1.0;
@@ -127,12 +132,19 @@ __device__ double apply_tile(const ChainView& c, int tile, const double2* __rest
         const double2 rv = make_double2(ch.x - res.x, ch.y - res.y);
         ea.r[o] = rv;
         return rv.x * rv.x + rv.y * rv.y;
-    } else {  // EPI_FORCE: in = x, res = y = M^dag x
+    } else if (EPI == EPI_FORCE) {  // in = x, res = y = M^dag x
         const double ph = ea.phi[o];
         // Im(x conj(y)) = x.y*y.x - x.x*y.y
         const double f = ph * ea.inv_dU + 2.0 * (src.y * res.x - src.x * res.y);
         if (ea.F) ea.F[o] = f;
         if (ea.pi) ea.pi[o] -= ea.kick * f;
+        return f * f;
+    } else {  // EPI_RATIO: in = x, res = y = M_g^dag x, d = y - x
+        const double2 ch = ea.chi[o];
+        const double dx = res.x - src.x, dy = res.y - src.y;
+        // Im(conj(d) chi) = d.x*chi.y - d.y*chi.x
+        const double f = -2.0 * (dx * ch.y - dy * ch.x);
+        ea.pi[o] -= ea.kick * f;
         return f * f;
     }
 }
@@ -158,14 +170,15 @@ struct CgResult {
     int status;
 };
 
-// Conjugate gradient on M M^dag (FP64), CG vectors in the chain workspace
+// Conjugate gradient on M M^dag (FP64; with hop_m1 != 0 on M_g M_g^dag, the
+// contraction scaled by 1 + hop_m1), CG vectors in the chain workspace
 // (r, p, q), from x = 0 or (warm) from the x given, whose residual
 // chi - M M^dag x then starts the iteration.  cis must hold exp(i phi).
 // Ends with the FP64 true residual, which leaves chi - M M^dag x in r and
 // M^dag x in q.
 __device__ inline bool cg_solve(const ChainView& c, Team& tm, const double2* chi, double2* x,
                          double tol, int max_iter, CgResult& res, Smem& sm,
-                         bool warm = false) {
+                         bool warm = false, double hop_m1 = 0.0) {
     double2 *r = c.r, *p = c.p, *q = c.q;
     double v1[1] = {0.0};
     HMC_TEAM_ELEMS(e, c, tm) {
@@ -192,6 +205,7 @@ __device__ inline bool cg_solve(const ChainView& c, Team& tm, const double2* chi
     ea.x = x;
     ea.r = r;
     ea.p = p;
+    ea.hop_m1 = hop_m1;
     if (warm) {
         // r = chi - M (M^dag x), p = r
         apply_team<true, EPI_STORE>(c, tm, x, q, ea, sm);

@@ -19,6 +19,8 @@ struct TrajArgs {
     int max_iter;
     double ru_delta;    // mixed path: reliable-update trigger
     int integrator;     // 0 leapfrog, 1 second-order minimum-norm (Omelyan)
+    double hb_gamma;    // mass preconditioning: hop factor g of M_g (hb_inner > 0)
+    int hb_inner;       // inner leapfrog steps per outer step (0: off)
 };
 
 // Molecular-dynamics schedule of a symmetric second-order integrator: kick
@@ -47,7 +49,9 @@ __host__ __device__ inline double md_kick(const TrajArgs& a, int m) {
 // Slots of ChainView::scalars written by the trajectory kernels.
 enum TrajSlot : int {
     kTrajDH = 0, kTrajH0, kTrajH1, kTrajU, kTrajAccept, kTrajIters, kTrajSolves,
-    kTrajRU, kTrajMaxRes, kTrajStatus, kTrajFp64Iters, kNumScalars = 16
+    kTrajRU, kTrajMaxRes, kTrajStatus, kTrajFp64Iters, kTrajItersOuter,
+    // 12 and 13 keep the mixed CG's segment state
+    kTrajSolvesOuter = 14, kNumScalars = 16
 };
 
 int launch_cis_f64(const ChainView& c, const double* phi, cudaStream_t s);

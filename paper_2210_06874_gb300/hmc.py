@@ -50,7 +50,8 @@ class hmc_params(ctypes.Structure):
                 ("tile_slices", ctypes.c_int), ("inner_ctas", ctypes.c_int),
                 ("operand_mode", ctypes.c_int), ("cluster_mode", ctypes.c_int),
                 ("integrator", ctypes.c_int), ("mu", ctypes.c_double),
-                ("ru_every", ctypes.c_int)]
+                ("ru_every", ctypes.c_int), ("hb_gamma", ctypes.c_double),
+                ("hb_inner", ctypes.c_int)]
 
 
 class hmc_cg_stats(ctypes.Structure):
@@ -64,7 +65,8 @@ class hmc_traj_out(ctypes.Structure):
                 ("u", ctypes.c_double), ("accept", ctypes.c_int),
                 ("cg_iterations", ctypes.c_int), ("cg_solves", ctypes.c_int),
                 ("reliable_updates", ctypes.c_int), ("max_true_residual", ctypes.c_double),
-                ("status", ctypes.c_int), ("fp64_iterations", ctypes.c_int)]
+                ("status", ctypes.c_int), ("fp64_iterations", ctypes.c_int),
+                ("cg_iterations_outer", ctypes.c_int), ("cg_solves_outer", ctypes.c_int)]
 
 
 _lib = None
@@ -157,6 +159,8 @@ class Params:
     integrator: int = 0
     mu: float = 0.0
     ru_every: int = 0
+    hb_gamma: float = 0.0
+    hb_inner: int = 0
 
     @property
     def V(self):
@@ -171,7 +175,8 @@ class Params:
                           self.traj_length, self.cg_tol, self.cg_max_iter, self.precision,
                           self.ru_delta, self.team_ctas, self.tile_slices,
                           self.inner_ctas, self.operand_mode, self.cluster_mode,
-                          self.integrator, self.mu, self.ru_every)
+                          self.integrator, self.mu, self.ru_every, self.hb_gamma,
+                          self.hb_inner)
 
 
 class Context:

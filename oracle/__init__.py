@@ -18,7 +18,9 @@ philox     Philox4x32-10 counter-based generator (Salmon et al., SC'11) and
 hasenbusch mass preconditioning (Hasenbusch 2001) with a two-level nested
            leapfrog (Sexton and Weingarten 1992): heavy operator, the two
            pseudofermions, their forces, the nested schedule, a trajectory
-observables zero-momentum single-particle correlator from one M^{-1} source
+observables zero-momentum single-particle correlator from one M^{-1} source;
+           staggered spin traces of M^{-1} (dense and by Z2 noise) and the
+           staggered susceptibility built from them
 
 Conventions (readings of the paper where it leaves a choice):
   * field phi is the product delta*phi_paper, so phases are exp(+i phi) and the

@@ -15,7 +15,9 @@ Stream layout shared with the GPU library (each side implements it on its own):
     u2 = ((x2 << 32 | x3) >> 11 + 0.5) * 2^-53
     Box-Muller: z0 = sqrt(-2 ln u1) cos(2 pi u2), z1 = sqrt(-2 ln u1) sin(2 pi u2)
 Streams: 0 momenta pi_e = z0; 1 pseudofermion noise rho_e = (z0 + i z1)/sqrt(2)
-(density exp(-rho^dag rho), §2); 2 the Metropolis uniform u1 of element 0.
+(density exp(-rho^dag rho), §2); 2 the Metropolis uniform u1 of element 0;
+3 the second pseudofermion's noise under mass preconditioning (as stream 1);
+4 Z2 noise 1 - 2 (x0 & 1) of the stochastic trace estimates.
 """
 import numpy as np
 
@@ -29,6 +31,7 @@ STREAM_MOMENTUM = 0
 STREAM_PSEUDOFERMION = 1
 STREAM_METROPOLIS = 2
 STREAM_HEAVY = 3          # second pseudofermion of mass preconditioning
+STREAM_Z2 = 4             # Z2 noise of the stochastic trace estimates
 
 
 def philox4x32_10(c0, c1, c2, c3, k0, k1):

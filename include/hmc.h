@@ -252,6 +252,36 @@ int hmc_trajectory(hmc_ctx* ctx, double* phi, uint64_t seed, uint64_t traj_index
 int hmc_correlator_k0(hmc_ctx* ctx, const double* phi, double tol, int max_iter, int precision,
                       void* C, hmc_cg_stats* stats, void* stream);
 
+/* Staggered spin traces of G = M[phi]^{-1} by Z2 noise, the ingredients of
+ * the staggered magnetisation that §2 names as an order parameter (its
+ * estimator is cited there, not printed).  With eps_x = +1 on sublattice A
+ * (x < V/2), -1 on B, on every slice:
+ *     T_s = tr(eps G),  T_u = tr(G),  T_ss = tr(eps G eps G).
+ * Sample k uses eta_k(e) = 1 - 2 (word0 & 1), word0 the first Philox word of
+ * element e = t V + x, stream 4, counter (e, 4, k, chain), key `seed`;
+ * v = M^{-1} eta_k and w = M^{-1} (eps v), each M^{-1} = M^dag (M M^dag)^{-1}
+ * (CG to tol in `precision`, then the FP64 M^dag); the sample's estimates
+ * are (eta^T eps v, eta^T v, eta^T eps w), unbiased for the three traces.
+ * In the particle-hole basis of §1 (spin up = particles, spin down = holes,
+ * whose propagator is conj(G) at mu = 0), Wick's theorem gives the staggered
+ * space-time susceptibility of the field, chi_s = (Re T_u - Re T_ss) / (2N),
+ * N = V Nt, which this call also returns.
+ *   n_noise  1 .. 2^20 samples
+ *   samples  device complex128 [n_noise][3] (T_s, T_u, T_ss per sample), or NULL
+ *   mean     device complex128 [4]: the sample means of T_s, T_u, T_ss, and
+ *            (chi_s of the means, 0)
+ *   stats    host: iterations, reliable updates and FP64 iterations summed
+ *            over the 2 n_noise solves, the largest true residual, the status
+ * Sums are FP64 in a fixed order (repeatable bit for bit).  A context with
+ * mu != 0 returns HMC_ERR_UNSUPPORTED (the holes' propagator is conj(G) only
+ * at mu = 0); solver failures return their status (e.g.
+ * HMC_ERR_CG_NOT_CONVERGED) and stop.  Allocates 5 V Nt + 3 n_noise complex
+ * doubles and 1536 doubles on `stream` for the call (stream-ordered) and
+ * synchronises `stream` before returning. */
+int hmc_spin_traces(hmc_ctx* ctx, const double* phi, int n_noise, uint64_t seed, uint32_t chain,
+                    double tol, int max_iter, int precision, void* samples, void* mean,
+                    hmc_cg_stats* stats, void* stream);
+
 /* ---- The printed operator, Eq. (2.2) -------------------------------------
  * The mixed-differencing (Brower-Rebbi-Schaich) fermion operator exactly as
  * Eq. (2.2) prints it, as a sparse stencil; no context needed.  With

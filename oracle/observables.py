@@ -45,6 +45,9 @@ def correlator_k0(E, phi):
 # N = V Nt, whose ensemble average is the space-time integrated staggered
 # spin correlation (its equal-time pairs depend on the time ordering the
 # discretisation gives equal-time products; they are 1/Nt of the sum).
+# At mu = 0 on the bipartite lattice (eps E eps = E^{-1}) the particle-hole
+# symmetry reads eps G eps = 1 - G^dag, so T_ss = T_u - tr(G^dag G) and
+# chi_s = |G|_F^2 / (2N); per real noise vector, T_u - T_ss = |M^{-1} eta|^2.
 # Stochastic estimates use Z2 noise eta_k = +-1 (the lowest bit of Philox
 # word 0 of element e, stream 4, trajectory counter k, the chain id):
 # eta^dag eps M^{-1} eta, eta^dag M^{-1} eta and eta^dag eps M^{-1} eps

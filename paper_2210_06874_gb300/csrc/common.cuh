@@ -43,7 +43,8 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 }
 
 enum : uint32_t { kStreamMomentum = 0, kStreamNoise = 1, kStreamMetropolis = 2,
-                  kStreamHeavy = 3 };   // 3: the heavy pseudofermion of mass preconditioning
+                  kStreamHeavy = 3,     // the heavy pseudofermion of mass preconditioning
+                  kStreamZ2 = 4 };      // Z2 noise of the stochastic trace estimates
 
 // Counter (element, stream, trajectory mod 2^32, chain), key = seed halves.
 __device__ __forceinline__ uint4 philox_draw(uint64_t seed, uint32_t stream, uint64_t traj,

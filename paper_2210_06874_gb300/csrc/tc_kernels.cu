@@ -38,8 +38,13 @@ struct TcCtx {
     // pre-split U (plain remainder) over bhi / blo with 128-row boxes
     CUtensorMap map_whi, map_wlo, map_uhi, map_ulo;
     int w_cg, w_apply, ns_wapply, csplit_apply;
-    // split-K tiles (operand_mode 5): the scaled split of E in 128-row boxes
+    // split-K tiles (operand_mode 5): the scaled split of E in 128-row boxes;
+    // standalone applications: the shape (C CTAs per cluster, ns slices per
+    // n-group, 0 if it does not fit) and the maps of the pre-split source
+    // (plain remainder) over bhi / blo with boxes of sk_nn(ns) rows
     CUtensorMap map_shi, map_slo;
+    int sk_C_apply, sk_ns_apply;
+    CUtensorMap map_skb_hi, map_skb_lo;
 };
 
 namespace tc {
@@ -430,6 +435,63 @@ __global__ void __launch_bounds__(NTHR, 1)
     cluster_barrier_all();   // every member's partial staged (release / acquire)
     if (*((volatile int*)c.status) == 0)
         tc_wepilogue(st, W, c.V, i0, t0, ns, src, 1.f, c.e_inv, epi, rank, csplit);
+    cluster_barrier_all();   // the partials stay until every member has read them
+    tc_teardown(st);
+}
+
+// Standalone application on split-K tiles (operand_mode 5): clusters of C
+// CTAs, cluster (ib, ng) = site block ib x n-group ng of ns target slices;
+// each CTA loads its 128 rows x K range of the scaled split of E by TMA
+// (before waiting for the split pre-pass, which it does not read), then the
+// pre-split source rows 2 t0 .. 2 t0 + Nn of its K range (plain FP16 hi and
+// lo, one power-of-two scale per target slice), one barrier per 64-wide K
+// chunk, and issues each chunk's MMAs as it lands.  The C partials of a
+// cluster are summed through distributed shared memory in rank order by the
+// owners of the outputs (deterministic); a last cluster barrier keeps every
+// member's shared memory alive until the others have read it.  E moves
+// from L2 once per application (not once per slice tile).
+template <bool DAG>
+__global__ void __launch_bounds__(NTHR, 1)
+    k_apply_sk(const __grid_constant__ CUtensorMap mhi, const __grid_constant__ CUtensorMap mlo,
+               const __grid_constant__ CUtensorMap bhi, const __grid_constant__ CUtensorMap blo,
+               ChainView c, int C, int ns, const float2* in, float2* out, const float* inv) {
+    extern __shared__ __align__(1024) uint8_t dyn[];
+    TcState st;
+    tc_setup(st, dyn, c.status);
+    const SkGeom g = sk_geom(blockIdx.x, C, ns, c.V, c.Nt, c.Vr, c.Vp);
+    TileBars& b = *st.bars;
+    const uint32_t cb = 2u * (uint32_t)g.Nn * 128u;   // bytes of one stacked B chunk
+    if (threadIdx.x == 0) {
+        const uint32_t bar = smem_u32(&b.res_full);
+        mbar_arrive_expect_tx(bar, (uint32_t)g.nch * kAChunkBytes);
+        for (int j = 0; j < g.nch; ++j) {
+            const uint32_t dst = smem_u32(st.base + (size_t)j * kAChunkBytes);
+            const int x = 16 * g.ks0 + KCH * j;   // a multiple of 16 elements
+            tma_load_2d(dst, &mhi, x, g.ib * TM, bar);
+            tma_load_2d(dst + kATileBytes, &mlo, x, g.ib * TM, bar);
+        }
+    }
+    // launched as a programmatic dependent of the split (see k_apply)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < g.nch; ++j) {
+            const uint32_t bar = smem_u32(&b.skb[j]);
+            const uint32_t dst = smem_u32(st.base + g.b_off + (size_t)j * cb);
+            const int x = 16 * g.ks0 + KCH * j;
+            mbar_arrive_expect_tx(bar, cb);
+            tma_load_2d(dst, &bhi, x, 2 * g.t0, bar);
+            tma_load_2d(dst + (uint32_t)g.Nn * 128u, &blo, x, 2 * g.t0, bar);
+        }
+        bool ok = mbar_wait(smem_u32(&b.res_full), 0, st.status);
+        for (int j = 0; j < g.nch && ok; ++j) {
+            ok = mbar_wait(smem_u32(&b.skb[j]), 0, st.status);
+            if (ok) sk_issue_chunk(st, g, j, smem_u32(st.base + g.b_off + (size_t)j * cb),
+                                   b.tmem_base);
+        }
+    }
+    Team none = {};
+    SkEpiOut<DAG> epi{in, out, c.cis_f, inv, c.e_inv, c.V, c.Nt};
+    sk_finish<true>(st, g, none, c.V, 1.f, epi);
     cluster_barrier_all();   // the partials stay until every member has read them
     tc_teardown(st);
 }
@@ -1316,6 +1378,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
+static bool splitk_shape(const hmc_ctx* c, int* C_out, int* ns_out);
+
 static bool make_map(CUtensorMap* m, void* base, int Vr, int Vp, int box_rows = tc::TM) {
     auto enc = encode_fn();
     if (!enc) return false;
@@ -1465,6 +1529,17 @@ int tc_ctx_init(hmc_ctx* c) {
             !make_map(&c->tc->map_ulo, c->tc->blo, c->tc->b_rows, v.Vp,
                       tc::wide_u_rows(c->tc->ns_wapply)))
             return HMC_ERR_CUDA;
+        // split-K standalone applications (operand_mode 5)
+        c->tc->sk_C_apply = 0;
+        c->tc->sk_ns_apply = 0;
+        int skC = 0, skns = 0;
+        if (c->params.operand_mode == 5 && splitk_shape(c, &skC, &skns)) {
+            if (!make_map(&c->tc->map_skb_hi, c->tc->bhi, c->tc->b_rows, v.Vp, tc::sk_nn(skns)) ||
+                !make_map(&c->tc->map_skb_lo, c->tc->blo, c->tc->b_rows, v.Vp, tc::sk_nn(skns)))
+                return HMC_ERR_CUDA;
+            c->tc->sk_C_apply = skC;
+            c->tc->sk_ns_apply = skns;
+        }
         const int split_smem = V * (int)sizeof(float2);
         for (const void* k : {(const void*)tc::k_split<false, false>,
                               (const void*)tc::k_split<true, false>,
@@ -1477,6 +1552,8 @@ int tc_ctx_init(hmc_ctx* c) {
     }
     const void* kernels[] = {(const void*)tc::k_apply<false>,
                              (const void*)tc::k_apply<true>,
+                             (const void*)tc::k_apply_sk<false>,
+                             (const void*)tc::k_apply_sk<true>,
                              (const void*)tc::k_apply_w<false>,
                              (const void*)tc::k_apply_w<true>,
                              (const void*)tc::k_cg<tc::kKindSite>,
@@ -1534,6 +1611,26 @@ int tc_apply(hmc_ctx* c, const double* phi, const float2* in, float2* out, bool 
     const ChainView& v = c->view;
     const size_t split_smem = (size_t)v.V * sizeof(float2);
     TcCtx* t = c->tc;
+    if (c->params.operand_mode == 5 && t->sk_C_apply > 0) {
+        int C = t->sk_C_apply, ns = t->sk_ns_apply;
+        const int grid = (v.Vr / tc::TM) * ((v.Nt + ns - 1) / ns) * C;
+        if (dag)
+            tc::k_split<true, true><<<v.Nt, tc::kSplitThreads, split_smem, s>>>(
+                phi, in, v.cis_f, t->bhi, t->blo, t->inv_col, v.V, v.Vp, v.Nt);
+        else
+            tc::k_split<false, true><<<v.Nt, tc::kSplitThreads, split_smem, s>>>(
+                phi, in, v.cis_f, t->bhi, t->blo, t->inv_col, v.V, v.Vp, v.Nt);
+        if (cudaGetLastError() != cudaSuccess) return HMC_ERR_CUDA;
+        ChainView vv = v;
+        const float2* inp = in;
+        float2* outp = out;
+        const float* invp = t->inv_col;
+        void* args[] = {&t->map_shi, &t->map_slo, &t->map_skb_hi, &t->map_skb_lo, &vv,
+                        &C, &ns, &inp, &outp, &invp};
+        return launch_dependent(
+            dag ? (const void*)tc::k_apply_sk<true> : (const void*)tc::k_apply_sk<false>, grid,
+            C, args, s);
+    }
     if (c->params.operand_mode == 4) {
         int W = t->w_apply, ns = t->ns_wapply, cs = t->csplit_apply;
         const int tiles = ((v.V + W - 1) / W) * ((v.Nt + ns - 1) / ns);

@@ -49,6 +49,8 @@ namespace hmc {
 namespace tc {
 
 constexpr int kSkMaxChunks = 4;      // K chunks of 64 per CTA (K range <= 256)
+static_assert(kSkMaxChunks <= (int)(sizeof(TileBars::skb) / sizeof(uint64_t)),
+              "one B barrier per chunk of a standalone application");
 constexpr int kSkMaxNn = 128;        // B rows per part (2 x slices of an n-group)
 constexpr int kSkMaxCluster = 8;
 
@@ -455,15 +457,17 @@ __device__ __forceinline__ void sk_build_and_issue(const TcState& st, const SkGe
 // outputs: epi.store(tt, i, ow, w) gets w[4] = (E u)(i .. i+3) of slice
 // t0 + tt (unscaled by 1/scale * 2^-eE), ow = the owner index of site i.
 // All threads call it; false if a bounded wait failed (status set).
-template <bool DAG, class Epi>
-__device__ __forceinline__ bool sk_apply(TcState& st, const SkGeom& g, Team& tcl,
-                                         const SkSrc& src, int V, int Nt, float scale,
-                                         float unscale, Epi& epi) {
+// The part of an application after the MMAs are issued: wait for the
+// accumulator, stage it, sync the cluster (HW: the hardware cluster barrier
+// of a standalone launch; else the bounded barrier of the CG team), sum the
+// owned outputs' partials and run the epilogue.
+template <bool HW, class Epi>
+__device__ __forceinline__ bool sk_finish(TcState& st, const SkGeom& g, Team& tcl, int V,
+                                          float unscale, Epi& epi) {
     TileBars& bars = *st.bars;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t tmem = bars.tmem_base;
     const int Nn = g.Nn;
-    sk_build_and_issue<DAG>(st, g, src, Nt, scale, tmem);
     // partial accumulator -> staging [column][128 rows] (FP32)
     bool ok = mbar_wait(smem_u32(&bars.acc_full), st.ntile & 1, st.status);
     st.ntile += 1;
@@ -487,8 +491,13 @@ __device__ __forceinline__ bool sk_apply(TcState& st, const SkGeom& g, Team& tcl
     }
     fence_before_sync();
     __syncthreads();
-    if (!ok) return false;
-    if (!sk_cluster_sync(tcl)) return false;
+    if constexpr (HW) {
+        cluster_barrier_all();   // every member's partial staged (release / acquire)
+        if (!ok) return false;
+    } else {
+        if (!ok) return false;
+        if (!sk_cluster_sync(tcl)) return false;
+    }
     // owned slices: sum the C partials in rank order, then the epilogue
     const uint32_t stg_s = smem_u32(stg);
     const int items = (g.so1 - g.so0) * (TM / 4);
@@ -539,6 +548,14 @@ __device__ __forceinline__ bool sk_apply(TcState& st, const SkGeom& g, Team& tcl
         epi.store(g.t0 + tt, i, tl * TM + i4, wv);
     }
     return true;
+}
+
+template <bool DAG, class Epi>
+__device__ __forceinline__ bool sk_apply(TcState& st, const SkGeom& g, Team& tcl,
+                                         const SkSrc& src, int V, int Nt, float scale,
+                                         float unscale, Epi& epi) {
+    sk_build_and_issue<DAG>(st, g, src, Nt, scale, st.bars->tmem_base);
+    return sk_finish<false>(st, g, tcl, V, unscale, epi);
 }
 
 // Owner vectors of a CTA in shared memory: FP32 complex arrays of g.own
@@ -655,6 +672,69 @@ struct SkEpiM {
 #pragma unroll
             for (int e = 0; e < 4; ++e)
                 if (i + e < V) r[o + e] = rs[e];
+        }
+    }
+};
+
+// Epilogue of a standalone application at (t, i .. i+3): with
+// w = (E u)_t unscaled by the source slice's inverse scale inv[t] 2^-eE,
+//     M:      out_t = in_t - s_t w                      (s_0 = -1)
+//     M^dag:  out_t = in_t - s_{t+1} e^{-i phi_t} w     (s_Nt = -1)
+template <bool DAG>
+struct SkEpiOut {
+    const float2* in;
+    float2* out;
+    const float2* cis;   // FP32 e^{i phi} (M^dag)
+    const float* inv;    // per target slice
+    float e_inv;
+    int V, Nt;
+    float4 c0, c1;
+    __device__ __forceinline__ void prefetch(int t, int i) {
+        if (!DAG) return;
+        const size_t o = (size_t)t * V + i;
+        if (i + 4 <= V) {
+            c0 = *reinterpret_cast<const float4*>(cis + o);
+            c1 = *reinterpret_cast<const float4*>(cis + o + 2);
+        } else {
+            const float2 a = cis[o], b = i + 1 < V ? cis[o + 1] : make_float2(1.f, 0.f);
+            const float2 d = i + 2 < V ? cis[o + 2] : make_float2(1.f, 0.f);
+            const float2 e = i + 3 < V ? cis[o + 3] : make_float2(1.f, 0.f);
+            c0 = make_float4(a.x, a.y, b.x, b.y);
+            c1 = make_float4(d.x, d.y, e.x, e.y);
+        }
+    }
+    __device__ __forceinline__ void store(int t, int i, int, const float2 (&w)[4]) {
+        const size_t o = (size_t)t * V + i;
+        const float u = inv[t] * e_inv;
+        const float sg = DAG ? ((t == Nt - 1) ? -1.f : 1.f) : ((t == 0) ? -1.f : 1.f);
+        const float2 ph[4] = {make_float2(c0.x, c0.y), make_float2(c0.z, c0.w),
+                              make_float2(c1.x, c1.y), make_float2(c1.z, c1.w)};
+        float2 a[4];
+        if (i + 4 <= V) {
+            const float4 a0 = *reinterpret_cast<const float4*>(in + o);
+            const float4 a1 = *reinterpret_cast<const float4*>(in + o + 2);
+            a[0] = make_float2(a0.x, a0.y);
+            a[1] = make_float2(a0.z, a0.w);
+            a[2] = make_float2(a1.x, a1.y);
+            a[3] = make_float2(a1.z, a1.w);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) a[e] = i + e < V ? in[o + e] : make_float2(0.f, 0.f);
+        }
+        float2 r[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            float2 wv = make_float2(w[e].x * u, w[e].y * u);
+            if (DAG) wv = cmulcf(ph[e], wv);
+            r[e] = make_float2(a[e].x - sg * wv.x, a[e].y - sg * wv.y);
+        }
+        if (i + 4 <= V) {
+            *reinterpret_cast<float4*>(out + o) = make_float4(r[0].x, r[0].y, r[1].x, r[1].y);
+            *reinterpret_cast<float4*>(out + o + 2) = make_float4(r[2].x, r[2].y, r[3].x, r[3].y);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (i + e < V) out[o + e] = r[e];
         }
     }
 };

@@ -63,6 +63,7 @@ struct TileBars {
     uint64_t wfull[4];            // slice-major ring (tc_wide.cuh): TMA bytes + producers
     uint64_t wempty[4];           // slice-major ring: MMA commit
     uint64_t wacc;                // slice-major tile: accumulator complete
+    uint64_t skb[4];              // split-K standalone application: B chunk j landed
     uint32_t tmem_base;
 };
 constexpr size_t kSmemBytes = kOperandBytes + sizeof(TileBars) + 1024;  // + alignment slack
@@ -343,6 +344,7 @@ __device__ inline void tc_setup(TcState& st, uint8_t* dyn, int* status) {
         }
         mbar_init(smem_u32(&b.acc_full), 1);
         mbar_init(smem_u32(&b.res_full), 1);
+        for (int j = 0; j < 4; ++j) mbar_init(smem_u32(&b.skb[j]), 1);
         for (int s = 0; s < 4; ++s) {
             mbar_init(smem_u32(&b.wfull[s]), 1 + kNumBWarps);
             mbar_init(smem_u32(&b.wempty[s]), 1);

@@ -99,6 +99,9 @@ SIGNATURES = {
                                      ctypes.c_int, ctypes.c_int, _P]),
     "hmc_correlator_k0": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                          _P, ctypes.POINTER(hmc_cg_stats), _P]),
+    "hmc_spin_traces": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
+                                       ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P,
+                                       ctypes.POINTER(hmc_cg_stats), _P]),
     "hmc_cg_solve_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P,
                                             ctypes.c_double, ctypes.c_int,
                                             ctypes.POINTER(hmc_cg_stats), _P]),
@@ -267,6 +270,23 @@ class Context:
                self.lib.hmc_correlator_k0(self._h, _ptr(phi), tol, max_iter, prec, _ptr(C),
                                           ctypes.byref(st), _stream()))
         return C, st
+
+    def spin_traces(self, phi, n_noise, seed, chain=0, tol=None, max_iter=None,
+                    prec=PREC_FP64):
+        """Z2-noise estimates of the staggered spin traces (hmc_spin_traces):
+        per-sample values complex128 [n_noise, 3] (T_s, T_u, T_ss), their
+        means with chi_s appended (complex128 [4]) and the summed CG stats."""
+        self._field(phi, "phi", torch.float64)
+        samples = torch.empty(n_noise, 3, dtype=torch.complex128, device=phi.device)
+        mean = torch.empty(4, dtype=torch.complex128, device=phi.device)
+        st = hmc_cg_stats()
+        tol = self.params.cg_tol if tol is None else tol
+        max_iter = self.params.cg_max_iter if max_iter is None else max_iter
+        _check("hmc_spin_traces",
+               self.lib.hmc_spin_traces(self._h, _ptr(phi), int(n_noise), int(seed), int(chain),
+                                        tol, max_iter, prec, _ptr(samples), _ptr(mean),
+                                        ctypes.byref(st), _stream()))
+        return samples, mean, st
 
     def force(self, phi, x, F=None):
         self._field(phi, "phi", torch.float64)

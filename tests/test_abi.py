@@ -99,3 +99,5 @@ def test_null_arguments_rejected(lib):
         hmc.HMC_ERR_BAD_ARG
     assert lib.hmc_rng_draw(0, 0, 0, 0, -1, None, None, None, None) == hmc.HMC_ERR_BAD_ARG
     assert lib.hmc_get_transfer_matrix(None, None, 0) == hmc.HMC_ERR_BAD_ARG
+    assert lib.hmc_spin_traces(None, None, 1, 0, 0, 1e-10, 10, 0, None, None, ctypes.byref(st),
+                               None) == hmc.HMC_ERR_BAD_ARG

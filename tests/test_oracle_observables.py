@@ -114,6 +114,32 @@ def test_particle_hole_symmetry_of_the_traces(L, Nt, beta):
     assert np.isclose(obs.spin_traces_exact(E, np.zeros((Nt, V)))[1], N / 2, rtol=1e-12)
 
 
+@pytest.mark.parametrize("L,Nt,beta,kappa", [(2, 6, 2.0, 1.0), (3, 4, 1.0, -0.6)])
+def test_particle_hole_identity_of_the_propagator(L, Nt, beta, kappa):
+    """mu = 0: eps h eps = -h makes eps E eps = E^{-1}; with the antiperiodic
+    sign this gives eps G eps = 1 - G^dag for every field, hence per real noise
+    vector Re(eta^T eps G eta) = sum(eps)/2 = 0 and T_u - T_ss = |G eta|^2
+    (chi_s = |G|_F^2 / (2N)).  With mu != 0 the identity fails."""
+    V, N = 2 * L * L, 2 * L * L * Nt
+    E = ops.transfer_matrix(lattice.hopping_matrix(L), beta / Nt * kappa)
+    phi = random_field(L, Nt, seed=L + Nt)
+    G = np.linalg.inv(ops.dense_M(E, phi))
+    eps = np.tile(obs.sublattice_signs(V), Nt)
+    assert np.allclose(eps[:, None] * G * eps[None, :], np.eye(N) - G.conj().T, atol=1e-12)
+    s = obs.spin_trace_samples(E, phi, 3, 8)
+    for k in range(3):
+        v = G @ obs.z2_noise(8, k, 0, Nt, V).ravel()
+        assert abs(s[k, 0].real) < 1e-10
+        assert np.isclose(s[k, 1] - s[k, 2], np.vdot(v, v), rtol=1e-12)
+    _, Tu, Tss = obs.spin_traces_exact(E, phi)
+    assert np.isclose(obs.staggered_susceptibility(Tu, Tss, N),
+                      np.linalg.norm(G) ** 2 / (2 * N), rtol=1e-12)
+    Emu = ops.transfer_matrix(lattice.hopping_matrix(L), beta / Nt * kappa, beta / Nt * 0.4)
+    Gmu = np.linalg.inv(ops.dense_M(Emu, phi))
+    assert not np.allclose(eps[:, None] * Gmu * eps[None, :], np.eye(N) - Gmu.conj().T,
+                           atol=1e-6)
+
+
 def test_traces_at_kappa_zero_depend_on_the_time_sum_only():
     """kappa = 0: a site's traces depend on its field only through
     Phi_x = sum_t phi_{x,t} (a diagonal unitary change of basis moves the

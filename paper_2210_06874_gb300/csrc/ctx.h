@@ -1,6 +1,7 @@
 // ctx.h -- the opaque hmc_ctx and the per-chain device view handed to kernels.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -33,9 +34,21 @@ struct ChainView {
     double *pi, *phi_old;       // double [Nt][V]
     // FP32 workspaces for the mixed path, float2 [Nt][V] each
     float2 *cis_f, *r_f, *p_f, *p2_f, *q_f, *x_f;
-    // split-K CG (operand_mode 5): G = E p' carried per target slice, and
-    // u = e^{i phi} q, the source of the M application
-    float2 *g_f, *u_f;
+    // split-K CG (operand_mode 5): the sources of its applications with a
+    // one-slice halo, rows [Nt + 2][V]: row t + 1 holds slice t, row 0 slice
+    // Nt - 1 and row Nt + 1 slice 0, so every n-group's shifted source
+    // slices are contiguous rows; u = e^{i phi} q (source of M) and r (source
+    // of M^dag); sk_maps: their TMA maps in global memory (CUtensorMap[2]:
+    // r, u; null when the context has no split-K shape)
+    float2 *g_f, *u_f, *rh_f;
+    // ... and their FP16 splits (plain remainder) at a team-uniform scale,
+    // written by the owners, rows [2 (Nt + 2)][Vp] (row 2h: Re, 2h + 1: Im
+    // of halo row h), in the order r hi, r lo, u hi, u lo
+    __half_raw* sk_b16;
+    // sk_maps: CUtensorMap[6] in global memory: [0] r, [1] u (FP32 halo
+    // rows), [2] r hi, [3] r lo, [4] u hi, [5] u lo (FP16, boxes of sk_nn(ns)
+    // rows, 128-byte swizzle); null when the context has no split-K shape
+    const void* sk_maps;
     unsigned long long* gslots; // sequence-numbered partial sums and totals (tc_splitk.cuh)
     // team synchronisation
     unsigned* bar;              // 2 words

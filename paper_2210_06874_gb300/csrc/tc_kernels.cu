@@ -618,9 +618,19 @@ __device__ __forceinline__ void cg_after_r(CgScalars& s, float rr_new) {
 // the FP32 residual (or, refresh, the FP64 residual, also written back as
 // FP32), p and G start at zero in the first segment of a solve and carry
 // over otherwise, x (the FP32 increment) starts at zero and is folded into
-// x64 by its owner at the end.  Returns the segment's end reason, or -1 if
-// a bounded wait failed.  Not inlined into the persistent kernels: the
-// iteration gets its own register budget.
+// x64 by its owner at the end.
+//
+// Each application: wait for the owners of this CTA's K range (their posted
+// words), copy and split the source with the scale from their largest
+// exponent, issue the MMAs; meanwhile warp 0 sums the norm that the previous
+// epilogue posted and thread 0 updates the scalars (alpha after |q|^2;
+// beta, or the end of the segment, after |r|^2); then stage the partial,
+// and, unless the segment ends, sync the cluster, reduce and run the
+// epilogue, which writes the next source and posts its norm.  The decision
+// to end the segment therefore comes after the next M^dag's MMAs are issued;
+// their result is drained and dropped.  Returns the segment's end reason,
+// or -1 if a bounded wait failed.  Not inlined into the persistent kernels:
+// the iteration gets its own register budget.
 __device__ __noinline__ int sk_segment(const ChainView& c, Team& ti, TcState& st,
                                        const PersistentArgs& pa, ClusterSync* ics,
                                        CgScalars& s_cg, bool refresh, bool first,
@@ -633,16 +643,35 @@ __device__ __noinline__ int sk_segment(const ChainView& c, Team& ti, TcState& st
     tcl.cs = ics;
     SkOwner ow;
     ow.init(st.base, g);
-    float2* rf = c.r_f;
+    // the CTAs whose posts this CTA waits for: owners of the M^dag source (r)
+    // and of the M source (u), and the other members of its cluster
+    __shared__ int s_own[2][kSkMaxOwners];
+    __shared__ int s_nown[2];
+    __shared__ unsigned s_mexp;
+    const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(c.sk_maps);
+    if (threadIdx.x == 0) {
+        s_nown[0] = sk_owner_list(g, c.V, c.Nt, true, s_own[0], ti.rank);
+        s_nown[1] = sk_owner_list(g, c.V, c.Nt, false, s_own[1], ti.rank);
+        if (s_nown[0] < 0 || s_nown[1] < 0 || !maps) set_status(ti.status, HMC_ERR_UNSUPPORTED);
+        if (maps)
+            for (int m = 0; m < 6; ++m)
+                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(maps + m)
+                             : "memory");
+    }
+    float2* rh = c.rh_f;   // r with the halo rows (source of M^dag)
+    float mx = 0.f;
     HMC_SK_OWNED(o, oi, g, c) {
         float2 rv;
         if (refresh) {
             const double2 d = c.r[o];
             rv = make_float2((float)d.x, (float)d.y);
-            rf[o] = rv;
         } else {
-            rv = rf[o];
+            rv = c.r_f[o];
         }
+        mx = fmaxf(mx, fmaxf(fabsf(rv.x), fabsf(rv.y)));
+        const int t = (int)(o / (size_t)c.V);
+        rh[o + c.V] = rv;                                        // row t + 1
+        if (t == 0) rh[o + (size_t)(c.Nt + 1) * c.V] = rv;      // row Nt + 1
         ow.r[oi] = rv;
         ow.x[oi] = make_float2(0.f, 0.f);
         if (first) {
@@ -650,31 +679,117 @@ __device__ __noinline__ int sk_segment(const ChainView& c, Team& ti, TcState& st
             ow.G[oi] = make_float2(0.f, 0.f);
         }
     }
-    __syncthreads();
-    while (s_cg.it < pa.max_iter) {
-        float scr, invr;
-        vector_scale_f(s_cg.rr, scr, invr);
-        SkSrc sr{rf, c.r, refresh, c.V};
-        SkEpiDag ed{ow, c.u_f, cisf, s_cg.beta, c.V, c.Nt, 0.f};
-        if (!sk_apply<true>(st, g, tcl, sr, c.V, c.Nt, scr, invr * c.e_inv, ed)) return -1;
-        float qq;
-        if (!gather_sum_f(ti, c.gslots, st.gseq, ed.acc, qq)) return -1;
-        refresh = false;
-        if (threadIdx.x == 0) cg_after_q(s_cg, qq);
-        __syncthreads();
-        if (s_cg.reason != 0) { reason = s_cg.reason; break; }
-        SkSrc su{c.u_f, nullptr, false, c.V};
-        SkEpiM em{ow, rf, s_cg.alpha, c.V, 0.f};
-        if (!sk_apply<false>(st, g, tcl, su, c.V, c.Nt, s_cg.sc, s_cg.inv * c.e_inv, em))
-            return -1;
-        float rr_new;
-        if (!gather_sum_f(ti, c.gslots, st.gseq, em.acc, rr_new)) return -1;
-        if (threadIdx.x == 0) {
-            cg_after_r(s_cg, rr_new);
-            if (s_cg.reason == 0 && s_cg.it >= pa.max_iter) s_cg.reason = kSegMaxIter;
+    sk_post(ti, c.gslots, ++st.gseq, 0.f, mx);   // r ready (no norm: beta is the caller's)
+    if (team_failed(ti)) return -1;
+    bool have_rr = false;
+    const int warp = threadIdx.x >> 5;
+    // Predicted operand exponents: s_pe[k] for the next source of kind k
+    // (0: r, 1: u) from the team's largest exponent of its last one (every
+    // CTA computes the same value from the same slots); s_pw[k]: the exponent
+    // the owners used for the FP16 split of the last posted source of kind
+    // k, or kNoPe if they wrote none (the segment's first r is FP32 only).
+    constexpr int kNoPe = -1000;
+    __shared__ int s_pe[2], s_pw[2];
+    if (threadIdx.x == 0) {
+        if (first) s_pe[0] = s_pe[1] = kNoPe;
+        s_pw[0] = s_pw[1] = kNoPe;
+    }
+    // (the post above ended with a block barrier; these are read after the next)
+    __half_raw* const b16 = c.sk_b16;
+    const size_t plane = (size_t)2 * (c.Nt + 2) * c.Vp;
+    // One application of kind `list` (0: M^dag, source r, halo rows t0 + 2 ..;
+    // 1: M, source u, rows t0 ..): wait for the owners' words of seq; take
+    // the owners' FP16 split by TMA when its exponent is known and the
+    // owners' largest component scaled by it is in [2^4, 2^15) (no overflow,
+    // full precision), else the FP32 source by TMA split here with the scale
+    // from the owners' exponent; issue the MMAs.  Warp 1 sums the norm of seq
+    // (into *out) and the team's largest exponent (into *gm) meanwhile.
+    auto contract = [&](int list, float* out, unsigned* gm, float& inv) -> bool {
+        if (warp == 0) {
+            unsigned m = 0;
+            const bool ok =
+                sk_wait_owners(ti, c.gslots, st.gseq, s_own[list], s_nown[list], 0u, m);
+            if ((threadIdx.x & 31) == 0) s_mexp = ok ? m : 0xffffffffu;
         }
         __syncthreads();
+        const unsigned mexp = s_mexp;
+        if (mexp == 0xffffffffu) return false;
+        SkSum ss;
+        if (warp == 1) sk_sum_begin(ti, c.gslots, st.gseq, ss);
+        const int pw = s_pw[list];
+        const int top = (int)mexp - 127 + pw;
+        const bool fast = b16 && pw != kNoPe && mexp != 0xffu && (mexp == 0u || (top >= 4 && top <= 14));
+        bool ok = true;
+        const int row0 = list == 0 ? g.t0 + 2 : g.t0;
+        if (fast) {
+            inv = __int_as_float((127 - pw) << 23);
+            sk_issue_b16(st, g, maps + 2 + 2 * list, maps + 3 + 2 * list, 2 * row0,
+                         st.bars->tmem_base);
+        } else {
+            float sc;
+            sk_scale(mexp, sc, inv);
+            sk_issue_source(st, g, maps + list, row0);
+            ok = sk_convert_and_issue(st, g, sc, st.bars->tmem_base);
+        }
+        if (ok && warp == 1) {
+            float v = 0.f;
+            unsigned gmx = 0;
+            const bool oks = sk_sum_end(ti, c.gslots, st.gseq, ss, v, gmx);
+            if ((threadIdx.x & 31) == 0) {
+                *out = oks ? v : __int_as_float(0x7fc00000);
+                *gm = gmx;
+            }
+        }
+        return ok;
+    };
+    // predicted exponent of the next source of a kind whose largest
+    // component had biased exponent gm: that component times 2^e in [2^12, 2^13)
+    auto predict = [](unsigned gm) -> int {
+        if (gm == 0u || gm == 0xffu) return kNoPe;
+        return max(-120, min(120, 12 - ((int)gm - 127)));
+    };
+    __shared__ float s_norm;
+    __shared__ unsigned s_gm;
+    while (s_cg.it < pa.max_iter) {
+        float inv;
+        // ---- M^dag p' (p' = r + beta p): contract r
+        if (!contract(0, &s_norm, &s_gm, inv)) return -1;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_pe[0] = predict(s_gm);
+            if (have_rr) {
+                cg_after_r(s_cg, s_norm);
+                if (s_cg.reason == 0 && s_cg.it >= pa.max_iter) s_cg.reason = kSegMaxIter;
+            }
+        }
+        if (!sk_stage(st, g, inv)) return -1;   // its barrier publishes s_cg, s_pe
+        if (team_failed(ti)) return -1;
+        if (have_rr && s_cg.reason != 0) { reason = s_cg.reason; break; }
+        const int pu = s_pe[1];
+        SkEpiDag ed{ow, c.u_f, pu != kNoPe ? b16 + 2 * plane : nullptr, b16 + 3 * plane,
+                    __int_as_float((127 + (pu != kNoPe ? pu : 0)) << 23), c.Vp,
+                    cisf, s_cg.beta, c.V, c.Nt, 0.f, 0.f};
+        if (!sk_reduce<false>(st, g, tcl, c.V, c.e_inv, ed)) return -1;
+        if (threadIdx.x == 0) s_pw[1] = b16 ? pu : kNoPe;
+        sk_post(ti, c.gslots, ++st.gseq, ed.acc, ed.mx);   // u ready, |q|^2
+        // ---- M q: contract u = e^{i phi} q
+        if (!contract(1, &s_norm, &s_gm, inv)) return -1;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_pe[1] = predict(s_gm);
+            cg_after_q(s_cg, s_norm);
+        }
+        if (!sk_stage(st, g, inv)) return -1;
+        if (team_failed(ti)) return -1;
         if (s_cg.reason != 0) { reason = s_cg.reason; break; }
+        const int pr = s_pe[0];
+        SkEpiM em{ow, rh, pr != kNoPe ? b16 : nullptr, b16 + plane,
+                  __int_as_float((127 + (pr != kNoPe ? pr : 0)) << 23), c.Vp,
+                  s_cg.alpha, c.V, c.Nt, 0.f, 0.f};
+        if (!sk_reduce<false>(st, g, tcl, c.V, c.e_inv, em)) return -1;
+        if (threadIdx.x == 0) s_pw[0] = b16 ? pr : kNoPe;
+        sk_post(ti, c.gslots, ++st.gseq, em.acc, em.mx);   // r ready, |r|^2
+        have_rr = true;
     }
     if (reason != kSegNonfinite) {
         HMC_SK_OWNED(o, oi, g, c) {
@@ -1393,6 +1508,22 @@ static bool make_map(CUtensorMap* m, void* base, int Vr, int Vp, int box_rows = 
            CUDA_SUCCESS;
 }
 
+// TMA map of a split-K source with halo rows: [rows][V] complex64 seen as
+// 8-byte integers (the bits are copied as they are), boxes of 64 sites x
+// box_rows rows, no swizzle, zero fill outside.
+static bool make_map_src(CUtensorMap* m, void* base, int rows, int V, int box_rows) {
+    auto enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)V, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)V * 8};
+    cuuint32_t box[2] = {(cuuint32_t)tc::KCH, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_INT64, 2, base, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
 // Smallest slices-per-tile in {8, 16, 32, 64} with at most `slots` tiles.
 static int pick_ns(int nti, int Nt, int slots) {
     int ns = 8;
@@ -1465,7 +1596,11 @@ int tc_ctx_init(hmc_ctx* c) {
     v.q_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
     v.x_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
     v.g_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
-    v.u_f = (float2*)dev_alloc(c, N * sizeof(float2), &ok);
+    const size_t Nh = (size_t)(v.Nt + 2) * v.V;   // split-K sources with the halo rows
+    v.u_f = (float2*)dev_alloc(c, Nh * sizeof(float2), &ok);
+    v.rh_f = (float2*)dev_alloc(c, Nh * sizeof(float2), &ok);
+    v.sk_b16 = nullptr;
+    v.sk_maps = nullptr;
     v.gslots = (unsigned long long*)dev_alloc(c, tc::kGatherSlots * sizeof(unsigned long long),
                                               &ok);
     if (!ok) return HMC_ERR_CUDA;
@@ -1539,6 +1674,24 @@ int tc_ctx_init(hmc_ctx* c) {
                 return HMC_ERR_CUDA;
             c->tc->sk_C_apply = skC;
             c->tc->sk_ns_apply = skns;
+            // the CG's sources: r and u with their halo rows, boxes of ns rows,
+            // and their FP16 splits, boxes of sk_nn(ns) rows
+            const int rows16 = 2 * (v.Nt + 2);
+            const size_t plane = (size_t)rows16 * v.Vp;
+            __half_raw* b16 = (__half_raw*)dev_alloc(c, 4 * plane * sizeof(__half), &okb);
+            if (!okb) return HMC_ERR_CUDA;
+            c->view.sk_b16 = b16;
+            CUtensorMap hm[6];
+            if (!make_map_src(&hm[0], c->view.rh_f, v.Nt + 2, V, skns) ||
+                !make_map_src(&hm[1], c->view.u_f, v.Nt + 2, V, skns))
+                return HMC_ERR_CUDA;
+            for (int q = 0; q < 4; ++q)
+                if (!make_map(&hm[2 + q], b16 + q * plane, rows16, v.Vp, tc::sk_nn(skns)))
+                    return HMC_ERR_CUDA;
+            void* dm = dev_alloc(c, sizeof(hm), &okb);
+            if (!okb || cudaMemcpy(dm, hm, sizeof(hm), cudaMemcpyHostToDevice) != cudaSuccess)
+                return HMC_ERR_CUDA;
+            c->view.sk_maps = dm;
         }
         const int split_smem = V * (int)sizeof(float2);
         for (const void* k : {(const void*)tc::k_split<false, false>,

@@ -24,10 +24,12 @@
 // memory; after a bounded cluster barrier, CTA rank r of the cluster sums the
 // C partials of its share of the n-group's slices through distributed
 // shared memory in rank order (deterministic) and runs the fused CG
-// epilogue.  The team's norms are summed by gather_sum_f: every CTA posts
-// its FP32 partial with a sequence number to a slot in global memory and
-// every CTA adds all slots in rank order (no atomics; the same bits on every
-// CTA).
+// epilogue.  Each CTA splits its source with its own power-of-two scale,
+// from the largest exponent its source's owners posted, and unscales its
+// partial when staging it.  The team's norms travel in the same posted
+// words (sequence-numbered slots in global memory) and are summed by every
+// CTA in rank order (no atomics; the same bits on every CTA), overlapping
+// the next application's copies and MMAs.
 //
 // The CG iteration uses M^dag's linearity (as the CUDA-core cluster mode):
 // with G = E p'_{t+1} carried per target slice, E p' = E r_{t+1} + beta G,
@@ -193,111 +195,199 @@ __device__ inline bool sk_cluster_sync(Team& tcl) {
     return team_barrier(tcl);
 }
 
-// Team sum of one FP32 value per thread over the inner team without
-// atomics.  Every CTA posts its fixed-order sum with the sequence number
-// seq to slot [seq & 1][rank]; CTA 0 waits (bounded) until every slot of
-// that buffer carries seq, adds them in rank order and posts the total with
-// seq to the result word [seq & 1]; every CTA waits (bounded) for that word.
-// Two buffers suffice: a CTA posts sync seq + 2 only after reading the
-// result of seq + 1, which CTA 0 writes only after every CTA has posted
-// seq + 1, each of them after reading the result of seq.  One CTA polling
-// all slots and the others one word each keeps the polling traffic on the
-// few L2 lines involved small (every CTA polling every slot saturated them
-// and slowed all other memory traffic).  Each post and the result publish
-// the poster's global writes before it (fence, then store).  Result on
-// every thread.
-constexpr int kPollBatch = 8;
-constexpr int kGatherSlots = 2 * kMaxTeam + 32;   // two slot buffers, two result lines
-__device__ inline bool gather_sum_f(const Team& ti, unsigned long long* slots, unsigned& seq,
-                                    float x, float& out) {
-    __shared__ float s_w[32];
-    __shared__ float s_tot;
-    __shared__ int s_ok;
+// Team words of the split-K iteration.  After each epilogue every CTA of
+// the inner team posts one 64-bit word to its slot [seq & 1][rank]:
+//     seq (24 bits) | max exponent (8 bits) | FP32 partial norm (32 bits),
+// the max exponent being the biased FP32 exponent of the largest |Re|, |Im|
+// of the source elements it has just written.  The post publishes those
+// writes (block barrier, fence, then the store), so it doubles as the
+// owner's "data ready" flag: a consumer waits only for the owners of its K
+// range, takes their largest exponent as its operand scale, and copies.
+// The norm is summed later, before the epilogue that needs it, by every
+// CTA reading all slots in rank order (no atomics; the same bits on every
+// CTA), so the sum overlaps the copies and the MMAs.  Two slot buffers
+// suffice: a CTA posts seq + 2 only after reading every slot of seq + 1,
+// which every CTA posts only after its own reads of seq are done.
+// Each slot has its own 128-byte line (every CTA reads every slot once per
+// sum; packed slots put all of those reads on a few lines).
+constexpr int kSlotStride = 16;   // 64-bit words
+constexpr int kGatherSlots = 2 * kMaxTeam * kSlotStride;
+__device__ __forceinline__ size_t sk_slot(unsigned seq, int rank) {
+    return ((size_t)(seq & 1u) * kMaxTeam + (size_t)rank) * kSlotStride;
+}
+
+__device__ __forceinline__ unsigned long long sk_word(unsigned seq, unsigned mexp, float part) {
+    return ((unsigned long long)(seq & 0xffffffu) << 40) |
+           ((unsigned long long)(mexp & 0xffu) << 32) | (unsigned long long)__float_as_uint(part);
+}
+__device__ __forceinline__ bool sk_word_is(unsigned long long w, unsigned seq) {
+    return (unsigned)(w >> 40) == (seq & 0xffffffu);
+}
+
+// Bounded polling: every 16th probe checks the team status and the time.
+__device__ __forceinline__ bool sk_poll_expired(const Team& ti, unsigned k, uint64_t& t0) {
+    if ((k & 15u) != 0) return false;
+    if (t0 == 0) t0 = global_ns();
+    if (team_failed(ti) || global_ns() - t0 > wait_limit_ns(ti.status)) {
+        if (!team_failed(ti)) set_status(ti.status, HMC_ERR_TIMEOUT);
+        return true;
+    }
+    return false;
+}
+
+// Post (all threads): the block's sum of `part` and max of `mx` under seq.
+__device__ inline void sk_post(const Team& ti, unsigned long long* slots, unsigned seq,
+                               float part, float mx) {
+    __shared__ float s_p[32], s_m[32];
+    // this thread's shared-memory writes (split operands, staged partial)
+    // before the TMA loads that will overwrite them after the post
+    fence_proxy_async();
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        part += __shfl_down_sync(0xffffffffu, part, o);
+        mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    if (lane == 0) s_w[warp] = x;
-    seq += 1u;
-    __syncthreads();
-    unsigned long long* buf = slots + (size_t)(seq & 1u) * kMaxTeam;
-    unsigned long long* res = slots + 2 * kMaxTeam + 16 * (seq & 1u);   // own 128-byte line
-    const unsigned long long tag = (unsigned long long)seq << 32;
-    if (warp == 0) {
-        if (lane == 0) {
-            float a = 0.f;
-            for (int w = 0; w < nw; ++w) a += s_w[w];
-            __threadfence();
-            *reinterpret_cast<volatile unsigned long long*>(buf + ti.rank) =
-                tag | (unsigned long long)__float_as_uint(a);
+    if (lane == 0) {
+        s_p[warp] = part;
+        s_m[warp] = mx;
+    }
+    __syncthreads();   // also: every thread's epilogue writes precede the fence below
+    if (threadIdx.x == 0) {
+        float a = 0.f, m = 0.f;
+        for (int w = 0; w < nw; ++w) {
+            a += s_p[w];
+            m = fmaxf(m, s_m[w]);
         }
-        __syncwarp();
-        bool ok = true;
-        uint64_t t0 = 0;
-        auto timed_out = [&](unsigned n) {
-            if ((n & 15u) != 0) return false;
-            if (t0 == 0) t0 = global_ns();
-            if (team_failed(ti) || global_ns() - t0 > wait_limit_ns(ti.status)) {
-                if (!team_failed(ti)) set_status(ti.status, HMC_ERR_TIMEOUT);
-                return true;
-            }
-            return false;
-        };
-        if (ti.rank == 0) {
-            const volatile unsigned long long* vb = buf;
-            float acc = 0.f;
-            for (int base = lane; base < ti.size && ok; base += 32 * kPollBatch) {
-                unsigned long long v[kPollBatch];
-#pragma unroll
-                for (int b = 0; b < kPollBatch; ++b) {
-                    const int r = base + 32 * b;
-                    v[b] = r < ti.size ? vb[r] : tag;
-                }
-                for (unsigned n = 1;; ++n) {
-                    bool all = true;
-#pragma unroll
-                    for (int b = 0; b < kPollBatch; ++b) all &= (v[b] >> 32) == (tag >> 32);
-                    if (all) break;
-                    if (timed_out(n)) { ok = false; break; }
-                    __nanosleep(32);
-#pragma unroll
-                    for (int b = 0; b < kPollBatch; ++b)
-                        if ((v[b] >> 32) != (tag >> 32)) v[b] = vb[base + 32 * b];
-                }
-#pragma unroll
-                for (int b = 0; b < kPollBatch; ++b)
-                    if (base + 32 * b < ti.size)
-                        acc += __uint_as_float((unsigned)(v[b] & 0xffffffffull));
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-            ok = __all_sync(0xffffffffu, ok);
-            if (lane == 0 && ok) {
-                __threadfence();
-                *reinterpret_cast<volatile unsigned long long*>(res) =
-                    tag | (unsigned long long)__float_as_uint(acc);
-            }
-        }
-        if (lane == 0) {
-            unsigned long long v = 0;
-            if (ok) {
-                const volatile unsigned long long* vr = res;
-                v = *vr;
-                for (unsigned n = 1; (v >> 32) != (tag >> 32); ++n) {
-                    if (timed_out(n)) { ok = false; break; }
-                    __nanosleep(32);
-                    v = *vr;
-                }
-            }
-            __threadfence();
-            s_tot = __uint_as_float((unsigned)(v & 0xffffffffull));
-            s_ok = ok ? 1 : 0;
+        const unsigned mexp = (__float_as_uint(m) >> 23) & 0xffu;
+        __threadfence();
+        *reinterpret_cast<volatile unsigned long long*>(slots + sk_slot(seq, ti.rank)) =
+            sk_word(seq, mexp, a);
+    }
+}
+
+// Team ranks of the CTAs that own the source elements of this CTA's K
+// range: the target slices of its n-group shifted to their source slices
+// (t + 1 for M^dag, t - 1 for M, cyclic), sites 16 ks0 .. min(16 ks1, V).
+// At most (C + 1) ranks per site block and 3 site blocks (K range <= 256
+// sites).  The other members of this CTA's cluster come first: they read
+// its staged partial through distributed shared memory, so its next source
+// may land there only after their posts.  Returns -1 beyond kSkMaxOwners.
+constexpr int kSkMaxOwners = 64;
+__device__ inline int sk_owner_list(const SkGeom& g, int V, int Nt, bool dag, int* list,
+                                    int team_rank) {
+    int n = 0;
+    const int cl0 = team_rank - g.rank;
+    for (int q = 0; q < g.C; ++q)
+        if (q != g.rank) list[n++] = cl0 + q;
+    const int k0 = 16 * g.ks0, k1 = min(16 * g.ks1, V);
+    if (k1 <= k0) return 0;
+    const int ib0 = k0 / TM, ib1 = (k1 - 1) / TM;
+    for (int tt = 0; tt < g.nsl; ++tt) {
+        int ts = g.t0 + tt + (dag ? 1 : -1);
+        ts = ts < 0 ? Nt - 1 : (ts >= Nt ? 0 : ts);
+        const int ngo = ts / g.ns, t0o = ngo * g.ns, nslo = min(g.ns, Nt - t0o), rr = ts - t0o;
+        int ro = 0;   // the owner: the last rank whose first owned slice is <= rr
+        while (ro + 1 < g.C && nslo * (ro + 1) / g.C <= rr) ++ro;
+        for (int ib = ib0; ib <= ib1; ++ib) {
+            const int rank = (ib * g.nng + ngo) * g.C + ro;
+            bool seen = false;
+            for (int q = 0; q < n; ++q) seen |= list[q] == rank;
+            if (seen) continue;
+            if (n == kSkMaxOwners) return -1;
+            list[n++] = rank;
         }
     }
-    __syncthreads();
-    out = s_tot;
-    const bool ok = s_ok != 0;
-    __syncthreads();
+    return n;
+}
+
+// Warp 0: wait (bounded) until the n ranks in `list` have posted seq and
+// return the largest max exponent among them; the lanes that saw a post
+// fence (acquire) before the block barrier that the caller runs next.
+// `mexp` starts from `own_mexp` (0 when the list covers every owner).
+__device__ inline bool sk_wait_owners(const Team& ti, const unsigned long long* slots,
+                                      unsigned seq, const int* list, int n, unsigned own_mexp,
+                                      unsigned& mexp) {
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+    unsigned m = own_mexp;
+    for (int q = lane; q < n && ok; q += 32) {
+        const volatile unsigned long long* p = slots + sk_slot(seq, list[q]);
+        unsigned long long w = *p;
+        uint64_t t0 = 0;
+        for (unsigned k = 1; !sk_word_is(w, seq); ++k) {
+            if (sk_poll_expired(ti, k, t0)) { ok = false; break; }
+            __nanosleep(32);
+            w = *p;
+        }
+        m = max(m, (unsigned)(w >> 32) & 0xffu);
+    }
+    __threadfence();
+    ok = __all_sync(0xffffffffu, ok);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    mexp = m;
     return ok;
+}
+
+// Warp 0: the sum of the partial norms of all team slots posted under seq,
+// in a fixed order (lane l adds ranks l, l + 32, ...; then a fixed shuffle
+// tree), so every CTA gets the same bits; also the largest max exponent
+// of the team (gmexp).  sk_sum_begin loads the first
+// kSumPre slots of each lane (their loads in flight while the caller does
+// other work); sk_sum_end polls those not yet posted, adds the rest of the
+// team and returns the sum on every lane.
+constexpr int kSumPre = 4;
+struct SkSum {
+    unsigned long long w[kSumPre];
+};
+__device__ __forceinline__ void sk_sum_begin(const Team& ti, const unsigned long long* slots,
+                                             unsigned seq, SkSum& ss) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int b = 0; b < kSumPre; ++b) {
+        const int r = lane + 32 * b;
+        ss.w[b] = r < ti.size ? *(const volatile unsigned long long*)(slots + sk_slot(seq, r))
+                              : sk_word(seq, 0u, 0.f);
+    }
+}
+__device__ inline bool sk_sum_end(const Team& ti, const unsigned long long* slots, unsigned seq,
+                                  SkSum& ss, float& out, unsigned& gmexp) {
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+    float acc = 0.f;
+    unsigned gm = 0;
+    for (int r = lane, b = 0; r < ti.size && ok; r += 32, ++b) {
+        unsigned long long w =
+            b < kSumPre ? ss.w[b] : *(const volatile unsigned long long*)(slots + sk_slot(seq, r));
+        uint64_t t0 = 0;
+        for (unsigned k = 1; !sk_word_is(w, seq); ++k) {
+            if (sk_poll_expired(ti, k, t0)) { ok = false; break; }
+            __nanosleep(64);
+            w = *(const volatile unsigned long long*)(slots + sk_slot(seq, r));
+        }
+        acc += __uint_as_float((unsigned)(w & 0xffffffffull));
+        gm = max(gm, (unsigned)(w >> 32) & 0xffu);
+    }
+    ok = __all_sync(0xffffffffu, ok);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_down_sync(0xffffffffu, acc, o);
+        gm = max(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+    }
+    out = __shfl_sync(0xffffffffu, acc, 0);
+    gmexp = gm;
+    return ok;
+}
+
+// Operand scale 2^e of a source whose largest component has biased
+// exponent mexp: largest |component| 2^e in [2^14, 2^15) (e = 0 for zero or
+// non-finite sources).
+__device__ __forceinline__ void sk_scale(unsigned mexp, float& scale, float& inv) {
+    int e = 0;
+    if (mexp != 0u && mexp != 0xffu) e = max(-120, min(120, 14 - ((int)mexp - 127)));
+    scale = __int_as_float((127 + e) << 23);
+    inv = __int_as_float((127 - e) << 23);
 }
 
 // B items (slice tt, 8-site group) per thread and chunk: a chunk has
@@ -457,18 +547,170 @@ __device__ __forceinline__ void sk_build_and_issue(const TcState& st, const SkGe
 // outputs: epi.store(tt, i, ow, w) gets w[4] = (E u)(i .. i+3) of slice
 // t0 + tt (unscaled by 1/scale * 2^-eE), ow = the owner index of site i.
 // All threads call it; false if a bounded wait failed (status set).
-// The part of an application after the MMAs are issued: wait for the
-// accumulator, stage it, sync the cluster (HW: the hardware cluster barrier
-// of a standalone launch; else the bounded barrier of the CG team), sum the
-// owned outputs' partials and run the epilogue.
-template <bool HW, class Epi>
-__device__ __forceinline__ bool sk_finish(TcState& st, const SkGeom& g, Team& tcl, int V,
-                                          float unscale, Epi& epi) {
+// Split-K CG source by TMA (thread 0): for every chunk j of this CTA's K
+// range, the box of 64 sites from 16 ks0 + 64 j and ns rows from row0 of
+// the halo layout (zeros past V and past the last row) into the space of
+// B chunk j, completing barrier skb[j].
+__device__ __forceinline__ void sk_issue_source(const TcState& st, const SkGeom& g,
+                                                const CUtensorMap* map, int row0) {
+    if (threadIdx.x != 0) return;
+    fence_proxy_async();
+    const uint32_t cb = 2u * (uint32_t)g.Nn * 128u;
+    const uint32_t bytes = (uint32_t)KCH * (uint32_t)g.ns * 8u;
+    for (int j = 0; j < g.nch; ++j) {
+        const uint32_t bar = smem_u32(&st.bars->skb[j]);
+        mbar_arrive_expect_tx(bar, bytes);
+        tma_load_2d(smem_u32(st.base + g.b_off + (size_t)j * cb), map, 16 * g.ks0 + KCH * j,
+                    row0, bar);
+    }
+}
+
+// Split two scaled FP32 values into FP16 pairs hi, lo with x = hi + lo:
+// Veltkamp's splitting with the constant 2^13 + 1 leaves hi with 11
+// significant bits (exact in FP16 for |x| < 2^16 down to the FP16 normal
+// range) and lo = x - hi exact in FP32, then rounded to FP16.  The products
+// are kept apart from the sums (no fused multiply-add may merge them).
+__device__ __forceinline__ void split_pair_v(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const float ta = __fmul_rn(a, 8193.f), tb = __fmul_rn(b, 8193.f);
+    const float ha = __fsub_rn(ta, __fsub_rn(ta, a)), hb = __fsub_rn(tb, __fsub_rn(tb, b));
+    const __half2 h = __floats2half2_rn(ha, hb);
+    const __half2 l = __floats2half2_rn(__fsub_rn(a, ha), __fsub_rn(b, hb));
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// All threads: chunk by chunk, wait for its source, split it in place with
+// `scale` and issue its MMAs (thread 0).  Item (slice tt, 8-site group grp)
+// is 64 bytes of raw row tt; its lane reads the four 16-byte pieces starting
+// at piece (grp >> 1) & 3 (the eight lanes of a quarter warp then hit eight
+// different bank groups) and writes each piece's two sites as four 32-bit
+// words (hi/lo x re/im) into the swizzled B rows (conflict-free as well).
+// False if a wait failed (status set; every thread returns together).
+__device__ __forceinline__ bool sk_convert_and_issue(TcState& st, const SkGeom& g, float scale,
+                                                     uint32_t tmem) {
+    const int Nn = g.Nn;
+    const uint32_t cb = 2u * (uint32_t)Nn * 128u;
+    const int per_chunk = g.nsl * 8;
+    const int kend = 16 * g.ks1;
+    const uint32_t phase = st.nskb & 1u;
+    st.nskb += 1;
+    for (int j = 0; j < g.nch; ++j) {
+        uint8_t* ch = st.base + g.b_off + (size_t)j * cb;
+        bool ok = mbar_wait(smem_u32(&st.bars->skb[j]), phase, st.status);
+        if (!__syncthreads_and(ok)) {
+            // MMAs of earlier chunks are in flight: commit them, so the
+            // teardown waits for them before it frees the accumulator
+            if (j > 0) {
+                if (threadIdx.x == 0) mma_commit(smem_u32(&st.bars->acc_full));
+                st.ntile += 1;
+            }
+            return false;
+        }
+        float4 v[kSkItems][4];
+        const float4* raw = reinterpret_cast<const float4*>(ch);
+#pragma unroll
+        for (int m = 0; m < kSkItems; ++m) {
+            const int r = threadIdx.x + m * NTHR;
+            if (r < per_chunk) {
+                const int tt = r >> 3, grp = r & 7, rot = (grp >> 1) & 3;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) v[m][e] = raw[tt * 32 + grp * 4 + ((e + rot) & 3)];
+            }
+        }
+        __syncthreads();   // every read of the raw chunk before the split overwrites it
+#pragma unroll
+        for (int m = 0; m < kSkItems; ++m) {
+            const int r = threadIdx.x + m * NTHR;
+            const int tt = r >> 3, grp = r & 7, rot = (grp >> 1) & 3;
+            const int kb = 16 * g.ks0 + KCH * j + 8 * grp;
+            if (r < per_chunk && kb < kend) {
+                const int jr = 2 * tt, ji = jr + 1;
+                uint8_t* hr = ch + jr * 128 + ((grp ^ (jr & 7)) << 4);
+                uint8_t* hm = ch + ji * 128 + ((grp ^ (ji & 7)) << 4);
+                uint8_t* lr = hr + (size_t)Nn * 128;
+                uint8_t* lm = hm + (size_t)Nn * 128;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int pc = ((e + rot) & 3) * 4;
+                    const float4 a = v[m][e];
+                    uint32_t h0, l0, h1, l1;
+                    split_pair_v(a.x * scale, a.z * scale, h0, l0);   // re of sites 2pc', +1
+                    split_pair_v(a.y * scale, a.w * scale, h1, l1);   // im
+                    *reinterpret_cast<uint32_t*>(hr + pc) = h0;
+                    *reinterpret_cast<uint32_t*>(lr + pc) = l0;
+                    *reinterpret_cast<uint32_t*>(hm + pc) = h1;
+                    *reinterpret_cast<uint32_t*>(lm + pc) = l1;
+                }
+            }
+        }
+        fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) sk_issue_chunk(st, g, j, smem_u32(ch), tmem);
+    }
+    return true;
+}
+
+// Sites i .. i+3 of halo row h of a source, split: FP16 hi and lo of the
+// values times sc (zeros for sites >= V) into rows 2h (Re) and 2h + 1 (Im)
+// of the hi and lo planes (row stride Vp; 8-byte stores).
+__device__ __forceinline__ void sk_store_b16(__half_raw* bh, __half_raw* bl, int Vp, int V, int h,
+                                             int i, const float2 (&v)[4], float sc) {
+    float re[4], im[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        re[e] = i + e < V ? v[e].x * sc : 0.f;
+        im[e] = i + e < V ? v[e].y * sc : 0.f;
+    }
+    uint32_t h0, l0, h1, l1, h2, l2, h3, l3;
+    split_pair_v(re[0], re[1], h0, l0);
+    split_pair_v(re[2], re[3], h1, l1);
+    split_pair_v(im[0], im[1], h2, l2);
+    split_pair_v(im[2], im[3], h3, l3);
+    const size_t ore = (size_t)(2 * h) * Vp + i, oim = ore + Vp;
+    *reinterpret_cast<uint2*>(bh + ore) = make_uint2(h0, h1);
+    *reinterpret_cast<uint2*>(bl + ore) = make_uint2(l0, l1);
+    *reinterpret_cast<uint2*>(bh + oim) = make_uint2(h2, h3);
+    *reinterpret_cast<uint2*>(bl + oim) = make_uint2(l2, l3);
+}
+
+// Split-K CG source already split by its owners (thread 0 only): for every
+// chunk j, the FP16 hi and lo boxes (64 sites from 16 ks0 + 64 j, sk_nn(ns)
+// rows from row16) straight into the swizzled B layout of chunk j, one
+// barrier per chunk; then chunk by chunk wait and issue the MMAs.  On a
+// failed wait the accumulator barrier is committed all the same (the
+// caller's wait for it then returns) and the status is set.
+__device__ __forceinline__ void sk_issue_b16(TcState& st, const SkGeom& g, const CUtensorMap* mhi,
+                                             const CUtensorMap* mlo, int row16, uint32_t tmem) {
+    const uint32_t phase = st.nskb & 1u;
+    st.nskb += 1;
+    if (threadIdx.x != 0) return;
+    const uint32_t cb = 2u * (uint32_t)g.Nn * 128u;
+    for (int j = 0; j < g.nch; ++j) {
+        const uint32_t bar = smem_u32(&st.bars->skb[j]);
+        const uint32_t dst = smem_u32(st.base + g.b_off + (size_t)j * cb);
+        const int x = 16 * g.ks0 + KCH * j;
+        mbar_arrive_expect_tx(bar, cb);
+        tma_load_2d(dst, mhi, x, row16, bar);
+        tma_load_2d(dst + (uint32_t)g.Nn * 128u, mlo, x, row16, bar);
+    }
+    for (int j = 0; j < g.nch; ++j) {
+        if (!mbar_wait(smem_u32(&st.bars->skb[j]), phase, st.status)) {
+            mma_commit(smem_u32(&st.bars->acc_full));
+            return;
+        }
+        sk_issue_chunk(st, g, j, smem_u32(st.base + g.b_off + (size_t)j * cb), tmem);
+    }
+}
+
+// After the MMAs are issued: wait for the accumulator and stage it in
+// shared memory as FP32 columns [column][128 rows], multiplied by
+// stage_scale (the inverse of this CTA's operand scale, exact: a power of
+// two).  All threads; false if the wait failed (status set).
+__device__ __forceinline__ bool sk_stage(TcState& st, const SkGeom& g, float stage_scale) {
     TileBars& bars = *st.bars;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t tmem = bars.tmem_base;
     const int Nn = g.Nn;
-    // partial accumulator -> staging [column][128 rows] (FP32)
     bool ok = mbar_wait(smem_u32(&bars.acc_full), st.ntile & 1, st.status);
     st.ntile += 1;
     fence_after_sync();
@@ -486,18 +728,29 @@ __device__ __forceinline__ bool sk_finish(TcState& st, const SkGeom& g, Team& tc
             tmem_ld16(tl + (uint32_t)(cb * 16), m);
             tmem_ld16(tl + (uint32_t)(Nn + cb * 16), l);
 #pragma unroll
-            for (int e = 0; e < 16; ++e) stg[(cb * 16 + e) * TM + row] = m[e] + l[e];
+            for (int e = 0; e < 16; ++e)
+                stg[(cb * 16 + e) * TM + row] = (m[e] + l[e]) * stage_scale;
         }
     }
     fence_before_sync();
     __syncthreads();
+    return ok;
+}
+
+// After sk_stage: sync the cluster (HW: the hardware cluster barrier of a
+// standalone launch, which every thread reaches; else the bounded barrier
+// of the CG team), then this CTA's owned outputs: the C partials summed in
+// rank order through distributed shared memory and multiplied by unscale,
+// then epi.store(t, i, owner index, w[4]).
+template <bool HW, class Epi>
+__device__ __forceinline__ bool sk_reduce(const TcState& st, const SkGeom& g, Team& tcl, int V,
+                                          float unscale, Epi& epi) {
     if constexpr (HW) {
         cluster_barrier_all();   // every member's partial staged (release / acquire)
-        if (!ok) return false;
     } else {
-        if (!ok) return false;
         if (!sk_cluster_sync(tcl)) return false;
     }
+    const float* stg = reinterpret_cast<const float*>(st.base + g.s_off);
     // owned slices: sum the C partials in rank order, then the epilogue
     const uint32_t stg_s = smem_u32(stg);
     const int items = (g.so1 - g.so0) * (TM / 4);
@@ -550,12 +803,33 @@ __device__ __forceinline__ bool sk_finish(TcState& st, const SkGeom& g, Team& tc
     return true;
 }
 
-template <bool DAG, class Epi>
-__device__ __forceinline__ bool sk_apply(TcState& st, const SkGeom& g, Team& tcl,
-                                         const SkSrc& src, int V, int Nt, float scale,
-                                         float unscale, Epi& epi) {
-    sk_build_and_issue<DAG>(st, g, src, Nt, scale, st.bars->tmem_base);
-    return sk_finish<false>(st, g, tcl, V, unscale, epi);
+template <bool HW, class Epi>
+__device__ __forceinline__ bool sk_finish(TcState& st, const SkGeom& g, Team& tcl, int V,
+                                          float unscale, Epi& epi) {
+    const bool ok = sk_stage(st, g, 1.f);
+    if constexpr (HW) {
+        // every thread reaches the hardware cluster barrier, failed or not
+        const bool r = sk_reduce<true>(st, g, tcl, V, unscale, epi);
+        return ok && r;
+    } else {
+        if (!ok) return false;
+        return sk_reduce<false>(st, g, tcl, V, unscale, epi);
+    }
+}
+
+// Four sites i .. i+3 of row `row` of a [rows][V] FP32 complex array
+// (16-byte stores when all four are in range).
+__device__ __forceinline__ void sk_store_halo(float2* a, int V, int row, int i,
+                                              const float2 (&v)[4]) {
+    float2* p = a + (size_t)row * V + i;
+    if (i + 4 <= V) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+        *reinterpret_cast<float4*>(p + 2) = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (i + e < V) p[e] = v[e];
+    }
 }
 
 // Owner vectors of a CTA in shared memory: FP32 complex arrays of g.own
@@ -586,11 +860,15 @@ struct SkOwner {
 // q in shared memory and writes u to global memory; sums |q|^2.
 struct SkEpiDag {
     SkOwner ow;
-    float2* u;
+    float2* u;       // halo rows [Nt + 2][V]
+    __half_raw *bh, *bl;   // FP16 split planes of u (null: not written)
+    float bscale;
+    int Vp;
     const float2* cis;
     float beta;
     int V, Nt;
-    float acc;
+    float acc;       // |q|^2 of the owned elements
+    float mx;        // largest |Re|, |Im| of the u written
     float4 c0, c1;   // prefetched phases
     __device__ __forceinline__ void prefetch(int t, int i) {
         const size_t o = (size_t)t * V + i;
@@ -606,7 +884,6 @@ struct SkEpiDag {
         }
     }
     __device__ __forceinline__ void store(int t, int i, int oi, const float2 (&w)[4]) {
-        const size_t o = (size_t)t * V + i;
         const float sg = (t == Nt - 1) ? -1.f : 1.f;
         const float2 ph[4] = {make_float2(c0.x, c0.y), make_float2(c0.z, c0.w),
                               make_float2(c1.x, c1.y), make_float2(c1.z, c1.w)};
@@ -622,16 +899,17 @@ struct SkEpiDag {
             ow.p[oi + e] = pv;
             ow.q[oi + e] = qv;
             us[e] = cmulf(ph[e], qv);
-            if (i + e < V) acc = fmaf(qv.x, qv.x, fmaf(qv.y, qv.y, acc));
+            if (i + e < V) {
+                acc = fmaf(qv.x, qv.x, fmaf(qv.y, qv.y, acc));
+                mx = fmaxf(mx, fmaxf(fabsf(us[e].x), fabsf(us[e].y)));
+            }
         }
-        if (i + 4 <= V) {
-            *reinterpret_cast<float4*>(u + o) = make_float4(us[0].x, us[0].y, us[1].x, us[1].y);
-            *reinterpret_cast<float4*>(u + o + 2) =
-                make_float4(us[2].x, us[2].y, us[3].x, us[3].y);
-        } else {
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (i + e < V) u[o + e] = us[e];
+        // halo layout: row t + 1; slice Nt - 1 also in row 0 (M's source of slice 0)
+        sk_store_halo(u, V, t + 1, i, us);
+        if (t == Nt - 1) sk_store_halo(u, V, 0, i, us);
+        if (bh) {
+            sk_store_b16(bh, bl, Vp, V, t + 1, i, us, bscale);
+            if (t == Nt - 1) sk_store_b16(bh, bl, Vp, V, 0, i, us, bscale);
         }
     }
 };
@@ -641,13 +919,16 @@ struct SkEpiDag {
 // and r in shared memory, writes r to global memory; sums |r|^2.
 struct SkEpiM {
     SkOwner ow;
-    float2* r;
+    float2* r;       // halo rows [Nt + 2][V]
+    __half_raw *bh, *bl;   // FP16 split planes of r (null: not written)
+    float bscale;
+    int Vp;
     float alpha;
-    int V;
-    float acc;
+    int V, Nt;
+    float acc;       // |r|^2 of the owned elements
+    float mx;        // largest |Re|, |Im| of the r written
     __device__ __forceinline__ void prefetch(int, int) {}
     __device__ __forceinline__ void store(int t, int i, int oi, const float2 (&w)[4]) {
-        const size_t o = (size_t)t * V + i;
         const float sg = (t == 0) ? -1.f : 1.f;
         float2 rs[4];
 #pragma unroll
@@ -662,16 +943,17 @@ struct SkEpiM {
             ow.x[oi + e] = xv;
             ow.r[oi + e] = rv;
             rs[e] = rv;
-            if (i + e < V) acc = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, acc));
+            if (i + e < V) {
+                acc = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, acc));
+                mx = fmaxf(mx, fmaxf(fabsf(rv.x), fabsf(rv.y)));
+            }
         }
-        if (i + 4 <= V) {
-            *reinterpret_cast<float4*>(r + o) = make_float4(rs[0].x, rs[0].y, rs[1].x, rs[1].y);
-            *reinterpret_cast<float4*>(r + o + 2) =
-                make_float4(rs[2].x, rs[2].y, rs[3].x, rs[3].y);
-        } else {
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (i + e < V) r[o + e] = rs[e];
+        // halo layout: row t + 1; slice 0 also in row Nt + 1 (M^dag's source of slice Nt - 1)
+        sk_store_halo(r, V, t + 1, i, rs);
+        if (t == 0) sk_store_halo(r, V, Nt + 1, i, rs);
+        if (bh) {
+            sk_store_b16(bh, bl, Vp, V, t + 1, i, rs, bscale);
+            if (t == 0) sk_store_b16(bh, bl, Vp, V, Nt + 1, i, rs, bscale);
         }
     }
 };

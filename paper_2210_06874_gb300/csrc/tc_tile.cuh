@@ -305,8 +305,9 @@ struct TcState {
                        // depth depends on the tile width, so each stage's
                        // barrier phases are counted on their own)
     uint32_t wtile;    // slice-major tiles so far
-    uint32_t gseq;     // split-K: team sums posted so far (gather_sum_f)
+    uint32_t gseq;     // split-K: team words posted so far (sk_post)
     int sk_loaded;     // split-K: this CTA's part of E' is resident
+    uint32_t nskb;     // split-K CG: applications whose sources came by TMA (skb phases)
     int* status;
     __device__ __forceinline__ uint8_t* a_hi(int kc, int s) const {
         return base + (mode == kResident ? kc : s) * kAChunkBytes;
@@ -335,6 +336,7 @@ __device__ inline void tc_setup(TcState& st, uint8_t* dyn, int* status) {
     st.wtile = 0;
     st.gseq = 0;
     st.sk_loaded = 0;
+    st.nskb = 0;
     st.status = status;
     TileBars& b = *st.bars;
     if (threadIdx.x == 0) {

@@ -420,14 +420,49 @@ def cpu_oracle_apply_rate(name, sample_s):
                       "as configured" % (n, name, dt)}
 
 
-def cpu_oracle_batch_rate(n_chains, sample_s):
-    """Time the oracle on the batched workload's chains in batch order, one
-    trajectory each from a cold start, until about sample_s seconds of work
-    are done (at least one chain): chains done / time."""
+def cpu_oracle_batch_rate(n_chains, sample_s, per_class=None, fields=None):
+    """The oracle on the batched workload.  With per_class (the GPU arm's FP64
+    sample: one chain per (L, Nt) class, its field in `fields`, its FP64 CG
+    iterations per trajectory): for every class, the oracle's seconds per
+    FP64 CG iteration on that chain's field and lattice (a bounded run split
+    evenly over the classes), times the iterations of one of its
+    trajectories, times the class's chain count; trajectories/s = chains /
+    sum.  Without it: oracle trajectories of the chains in batch order from a
+    cold start until about sample_s seconds of work are done."""
     import numpy as np
     from oracle import hmc as ohmc, lattice, operators as ops
     from paper_2210_06874_gb300 import synth
     specs = synth.batch256(n_chains=n_chains)
+    if per_class:
+        t0 = time.perf_counter()
+        share = sample_s / len(per_class)
+        total_s, parts = 0.0, []
+        for pc in per_class:
+            c = specs[pc["sampled_chain"]]
+            V, delta = 2 * c["L"] ** 2, c["beta"] / c["Nt"]
+            E = ops.transfer_matrix(lattice.hopping_matrix(c["L"]), delta * c["kappa"])
+            phi = fields[pc["sampled_chain"]]
+            rho = synth.complex_gaussian(pc["sampled_chain"] + 11, c["Nt"], V) / np.sqrt(2.0)
+            chi = ops.apply_M(E, phi, rho)
+            t1 = time.perf_counter()
+            _, it0, _ = ohmc.cg_solve(E, phi, chi, tol=1e-300, max_iter=3)
+            per = (time.perf_counter() - t1) / max(it0, 1)
+            cap = max(3, int(share / per))
+            t1 = time.perf_counter()
+            _, it, _ = ohmc.cg_solve(E, phi, chi, tol=1e-300, max_iter=cap)
+            per = (time.perf_counter() - t1) / max(it, 1)
+            total_s += per * pc["cg_iterations"] * pc["chains"]
+            parts.append("L%d Nt%d: %d its x %.3f ms" % (pc["L"], pc["Nt"], pc["cg_iterations"],
+                                                           1e3 * per))
+        dt = time.perf_counter() - t0
+        return {"value": n_chains / total_s, "unit": "trajectories/s", "cores": os.cpu_count(),
+                "kind": "oracle",
+                "sample": "per (L, Nt) class: oracle FP64 CG iterations timed on the sampled "
+                          "chain's field after the timed steps (%.1f s in all), scaled by that "
+                          "chain's FP64 CG iterations per trajectory on the GPU's FP64 path and "
+                          "by the class's chain count (%d classes, %d chains; %s); NumPy FP64, "
+                          "BLAS threads as configured"
+                          % (dt, len(per_class), n_chains, "; ".join(parts))}
     t0 = time.perf_counter()
     n = 0
     for i, c in enumerate(specs):
@@ -629,6 +664,8 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    phi_start = phi.clone()   # the e2e leg replays the same trajectories from here
+    traj_start = traj
     clocks.start()
     t_wall = time.perf_counter()
     total_ms, outs = 0.0, []
@@ -651,24 +688,31 @@ def run_ours(args):
     ms_per_step = total_ms / args.steps
 
     # end to end through the public API with host buffers: pinned phi in,
-    # trajectory, phi and the trajectory record back to the host
+    # trajectory, phi and the trajectory record back to the host.  The chain
+    # is deterministic (counter-based generator), so starting again from the
+    # field at the start of the timed region with the same trajectory
+    # indices repeats exactly the timed trajectories (same CG work).
     phi_host = torch.empty((Nt, V), dtype=torch.float64, pin_memory=True)
-    phi_host.copy_(phi.cpu())
+    phi_host.copy_(phi_start.cpu())
     back = torch.empty_like(phi_host)
     torch.cuda.synchronize()
-    e2e_steps = max(2, min(args.steps, 5))
-    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s.record(stream)
+    e2e_steps = args.steps
+    traj = traj_start
+    e2e_ms = 0.0
     for _ in range(e2e_steps):
+        flush_l2(flush, flush_acc)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
         phi.copy_(phi_host, non_blocking=True)
         out = ctx.trajectory(phi, seed, traj, rank, allow_not_converged=True)
         back.copy_(phi, non_blocking=True)
         stream.synchronize()
         phi_host.copy_(back)
+        e.record(stream)
+        e.synchronize()
+        e2e_ms += s.elapsed_time(e)
         traj += 1
-    e.record(stream)
-    e.synchronize()
-    e2e_ms = s.elapsed_time(e) / e2e_steps
+    e2e_ms /= e2e_steps
     h2d = Nt * V * 8
     d2h = Nt * V * 8 + 8 * 16
 
@@ -738,7 +782,9 @@ def run_ours(args):
         "mean_abs_dH": statistics.mean(abs(o.dH) for o in outs),
         "max_true_residual": max(o.max_true_residual for o in outs),
         "e2e": {"value": world / (e2e_ms * 1e-3), "unit": "trajectories/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "how": "the timed trajectories again (same start field and indices), "
+                       "phi from pinned host memory in and back every trajectory"},
         "gpu_launches": args.steps,
         "roofline": roof,
         "clocks": clk,
@@ -1040,6 +1086,7 @@ def run_batch(args):
     clocks = ClockSampler(local_rank)
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
+    phi_start, traj_start = phi.clone(), traj   # the e2e leg replays the timed steps
     clocks.start()
     total_ms, outs = 0.0, []
     for _ in range(args.steps):
@@ -1056,23 +1103,28 @@ def run_batch(args):
     # end to end through the public API with host buffers: every chain's
     # field in from pinned host memory, one batched trajectory, the fields
     # back (the per-chain records come back inside the call)
+    # (the same steps again from the same fields and trajectory indices: the
+    # chains are deterministic, so the work is the timed work)
+    phi_end = phi.clone()
     phi_host = torch.empty(b.total, dtype=torch.float64, pin_memory=True)
-    phi_host.copy_(phi.cpu())
+    phi_host.copy_(phi_start.cpu())
     back = torch.empty_like(phi_host)
     torch.cuda.synchronize()
-    e2e_steps = max(2, min(args.steps, 3))
+    e2e_steps = args.steps
+    t_e2e = traj_start
     s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     s.record(stream)
     for _ in range(e2e_steps):
         phi.copy_(phi_host, non_blocking=True)
-        b.trajectory(phi, seed, traj, allow_failure=True)
+        b.trajectory(phi, seed, t_e2e, allow_failure=True)
         back.copy_(phi, non_blocking=True)
         stream.synchronize()
         phi_host.copy_(back)
-        traj += 1
+        t_e2e += 1
     e.record(stream)
     e.synchronize()
     e2e_value = world * n / (s.elapsed_time(e) / e2e_steps * 1e-3)
+    phi.copy_(phi_end)
     e2e_bytes = b.total * 8
     # loop of single-chain launches over the same chains (first K_loop chains)
     n_loop = min(n, args.loop_chains)
@@ -1110,6 +1162,33 @@ def run_batch(args):
         e.record(stream)
         e.synchronize()
         loop64_ms = s.elapsed_time(e)
+    # the plain FP64 GPU path over the whole workload, estimated per class:
+    # one FP64 trajectory of the first chain of every (L, Nt) class from its
+    # current field (same cg_tol), weighted by the class's chain count
+    classes = {}
+    for i, p in enumerate(plist):
+        classes.setdefault((p.L, p.Nt), []).append(i)
+    per_class = []
+    est64_ms = 0.0
+    if not args.no_fp64_arm:
+        for (L_, Nt_), idx in sorted(classes.items()):
+            i = idx[0]
+            pc = hmc.Params(**{**plist[i].__dict__, "precision": hmc.PREC_FP64,
+                               "team_ctas": 0, "inner_ctas": 0, "tile_slices": 0,
+                               "operand_mode": 0})
+            c64 = hmc.Context(pc)
+            f = b.view(phi, i).clone()
+            torch.cuda.synchronize()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            o64 = c64.trajectory(f, seed, traj + 3, chain=i, allow_not_converged=True)
+            e.record(stream)
+            e.synchronize()
+            ms = s.elapsed_time(e)
+            est64_ms += ms * len(idx)
+            per_class.append({"L": L_, "Nt": Nt_, "chains": len(idx), "sampled_chain": i,
+                              "fp64_ms": ms, "cg_iterations": o64.cg_iterations})
+            del c64
     # the mixed loop over exactly those chains
     loop_mixed_same_ms = 0.0
     if n64 > 0 and n_loop >= n64:
@@ -1143,6 +1222,14 @@ def run_batch(args):
         "loop_of_single_chain_launches": {
             "chains": n_loop, "ms": loop_ms,
             "trajectories_per_s": n_loop / (loop_ms * 1e-3) if loop_ms else None},
+        "fp64_whole_workload_est": {
+            "trajectories_per_s": n / (est64_ms * 1e-3) if est64_ms else None,
+            "mixed_batched_over_fp64": value / (n / (est64_ms * 1e-3)) if est64_ms else None,
+            "how": "plain FP64 GPU path (hmc_trajectory, precision FP64, one chain per "
+                   "launch, same cg_tol 1e-10 FP64 true residual): one trajectory of one "
+                   "chain per (L, Nt) class from its field after the timed steps, "
+                   "times the class's chain count, summed",
+            "classes": per_class} if est64_ms else None,
         "loop_of_single_chain_launches_fp64": {
             "chains": n64, "ms": loop64_ms,
             "trajectories_per_s": n64 / (loop64_ms * 1e-3) if loop64_ms else None,
@@ -1162,7 +1249,10 @@ def run_batch(args):
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_oracle_batch_rate(args.chains, args.cpu_sample_s)
+        flds = {pc["sampled_chain"]: b.view(phi, pc["sampled_chain"]).cpu().numpy()
+                for pc in per_class}
+        line["cpu_baseline"] = cpu_oracle_batch_rate(args.chains, args.cpu_sample_s,
+                                                     per_class or None, flds)
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -108,10 +108,14 @@ __device__ inline SkGeom sk_geom(int team_rank, int C, int ns, int V, int Nt, in
     g.nch = sk_chunks(g.ks1 - g.ks0);
     g.so0 = g.nsl * g.rank / C;
     g.so1 = g.nsl * (g.rank + 1) / C;
-    g.b_off = (uint32_t)g.nch * kAChunkBytes;
-    const uint32_t bbytes = (uint32_t)g.nch * 2u * (uint32_t)g.Nn * 128u;
+    // The layout follows the largest chunk count of the cluster, not this
+    // CTA's own: the members read each other's staged partials at this
+    // CTA's offsets (distributed shared memory), so the offsets must agree.
+    const int nchx = sk_chunks((KS + C - 1) / C);
+    g.b_off = (uint32_t)nchx * kAChunkBytes;
+    const uint32_t bbytes = (uint32_t)nchx * 2u * (uint32_t)g.Nn * 128u;
     g.s_off = bbytes >= (uint32_t)g.Nn * TM * 4u ? g.b_off : g.b_off + bbytes;
-    g.o_off = (uint32_t)sk_smem_bytes(g.nch, g.Nn);
+    g.o_off = (uint32_t)sk_smem_bytes(nchx, g.Nn);
     g.own = (g.so1 - g.so0) * TM;
     (void)Vp;
     return g;

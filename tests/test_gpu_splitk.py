@@ -42,6 +42,8 @@ def test_splitk_cg_matches_oracle(L, Nt, beta, U, C, ns):
     tphi, tchi = torch.from_numpy(phi).to(DEV), torch.from_numpy(chi).to(DEV)
     x, st = ctx.cg_solve(tphi, tchi, tol=1e-10, prec=hmc.PREC_MIXED)
     assert st.status == hmc.HMC_OK and st.true_residual <= 1e-10
+    # the FP32 iteration itself converged (no switch to FP64 CG after a stall)
+    assert st.fp64_iterations == 0
     xo, _, _ = ohmc.cg_solve(oracle_E(L, Nt, beta), phi, chi, tol=1e-14, max_iter=100000)
     assert rel(x.cpu().numpy(), xo) < 1e-8
     # deterministic: the same solve gives the same bits
@@ -94,7 +96,8 @@ def test_splitk_l24_matches_fp64_path(C, ns):
 # for the largest element error against the largest element.
 APPLY_SIZES = [(3, 8, 0, 0), (3, 9, 0, 0), (5, 13, 0, 0), (6, 32, 0, 0), (7, 9, 0, 0),
                (6, 1, 0, 0), (9, 48, 0, 0), (12, 64, 0, 0), (24, 96, 0, 0), (12, 64, 8, 32),
-               (9, 48, 4, 20), (24, 96, 8, 0), (24, 96, 6, 32)]
+               (9, 48, 4, 20), (24, 96, 8, 0), (24, 96, 6, 32), (12, 16, 4, 0),
+               (12, 64, 4, 0), (24, 96, 7, 40)]
 
 
 @pytest.mark.parametrize("L,Nt,C,ns", APPLY_SIZES)
@@ -118,3 +121,27 @@ def test_splitk_apply_matches_oracle(L, Nt, C, ns, mu):
         assert np.abs(got - want).max() < 2e-6 * np.abs(want).max(), dag
         again = f(tphi, psi, prec=hmc.PREC_MIXED).cpu().numpy()
         assert np.array_equal(got, again)
+
+
+# Clusters whose CTAs hold different numbers of K chunks (e.g. V = 288 split
+# over 4 CTAs: 4, 5, 4 and 5 steps of 16 sites, 1 or 2 chunks of 64): the
+# members read each other's staged partials, so their shared-memory layout
+# must agree.  The FP32 iteration must converge on its own (no FP64
+# fallback) in about as many iterations as the FP64 CG.
+@pytest.mark.parametrize("L,Nt,C,ns", [(12, 16, 4, 0), (12, 32, 4, 0), (12, 64, 4, 0),
+                                       (12, 48, 4, 0), (9, 16, 4, 0), (24, 96, 8, 0),
+                                       (12, 64, 6, 0)])
+def test_splitk_cg_converges_in_fp32(L, Nt, C, ns):
+    V = 2 * L * L
+    beta = Nt / 8
+    phi = synth.gaussian_field(L * 7 + Nt, Nt, V, beta / Nt * 3.9, scale=0.3)
+    chi = synth.complex_gaussian(L * 7 + Nt + 1, Nt, V)
+    tphi, tchi = torch.from_numpy(phi).to(DEV), torch.from_numpy(chi).to(DEV)
+    ctx = hmc.Context(hmc.Params(L=L, Nt=Nt, beta=beta, U=3.9, precision=hmc.PREC_MIXED,
+                                 operand_mode=5, inner_ctas=C, tile_slices=ns))
+    x, st = ctx.cg_solve(tphi, tchi, tol=1e-10, prec=hmc.PREC_MIXED)
+    assert st.status == hmc.HMC_OK and st.true_residual <= 1e-10
+    assert st.fp64_iterations == 0
+    x64, st64 = ctx.cg_solve(tphi, tchi, tol=1e-10, prec=hmc.PREC_FP64)
+    assert st.iterations <= 1.3 * st64.iterations + 20
+    assert rel(x.cpu().numpy(), x64.cpu().numpy()) < 1e-8

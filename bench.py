@@ -80,6 +80,9 @@ def parse():
     ap.add_argument("--no-fp64-arm", action="store_true",
                     help="trajectory mode, mixed: skip the plain FP64 GPU path's solve")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--no-batch-line", action="store_true",
+                    help="default workload: skip the batched workload's comparison that the "
+                         "line carries as its batch256 object")
     ap.add_argument("--operand-mode", type=int, default=None, choices=[0, 1, 2, 3, 4, 5],
                     help="operand_mode of the mixed path instead of the autotuner's choice "
                          "(1 site-major tiles, 3 CUDA-core cluster mode, 4 slice-major "
@@ -447,7 +450,9 @@ def cpu_oracle_batch_rate(n_chains, sample_s, per_class=None, fields=None):
             t1 = time.perf_counter()
             _, it0, _ = ohmc.cg_solve(E, phi, chi, tol=1e-300, max_iter=3)
             per = (time.perf_counter() - t1) / max(it0, 1)
-            cap = max(3, int(share / per))
+            # at most a quarter of the dimension: on small lattices CG would
+            # otherwise reach the exact solution and divide by a zero norm
+            cap = max(3, min(int(share / per), V * c["Nt"] // 4))
             t1 = time.perf_counter()
             _, it, _ = ohmc.cg_solve(E, phi, chi, tol=1e-300, max_iter=cap)
             per = (time.perf_counter() - t1) / max(it, 1)
@@ -825,6 +830,9 @@ def run_ours(args):
                 line["cpu_baseline"]["single_thread"] = cpu_oracle_rate_single_thread(
                     name, prec, min(args.cpu_sample_s, 10.0), phi_np=phi_np,
                     integrator=args.integrator, n_md=params.n_md)
+    if world == 1 and name == "l24_nt96" and prec == "mixed" and not args.no_batch_line:
+        # the spec comparison on the batched workload, in the same line
+        line["batch256"] = batch_summary(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -1032,7 +1040,7 @@ def run_cg(args):
         print(json.dumps(line), flush=True)
 
 
-def run_batch(args):
+def run_batch(args, emit=True):
     """Batched workload: many chains of uneven size, one persistent launch per
     trajectory of every chain (hmc_batch_trajectory); value = aggregate
     trajectories/s.  Also times the same chains as a loop of single-chain
@@ -1253,8 +1261,38 @@ def run_batch(args):
                 for pc in per_class}
         line["cpu_baseline"] = cpu_oracle_batch_rate(args.chains, args.cpu_sample_s,
                                                      per_class or None, flds)
-    if rank == 0:
+    if rank == 0 and emit:
         print(json.dumps(line), flush=True)
+    return line
+
+
+def batch_summary(args):
+    """The batched workload's comparison, run after the default single-chain
+    line on one GPU: the batched mixed form against the plain FP64 GPU path
+    over the same 256 chains (a few steps; failures are reported, not
+    raised)."""
+    import copy
+    b_args = copy.copy(args)
+    b_args.steps, b_args.warmup, b_args.therm = 3, 1, None
+    b_args.cpu_sample_s = min(args.cpu_sample_s, 10.0)
+    try:
+        d = run_batch(b_args, emit=False)
+    except Exception as e:   # an extra of the default line: never fail the bench on it
+        return {"workload": "batch%d" % args.chains, "unavailable": str(e)[:300]}
+    f = d.get("fp64_whole_workload_est") or {}
+    out = {"workload": d["config"]["workload"], "metric": "aggregate trajectories/s",
+           "value": d["value"], "unit": d["unit"], "steps": d["steps"],
+           "ms_per_step": d["ms_per_step"], "e2e": d["e2e"],
+           "fp64_whole_workload_trajectories_per_s": f.get("trajectories_per_s"),
+           "mixed_batched_over_fp64": f.get("mixed_batched_over_fp64"),
+           "fp64_how": f.get("how"), "statuses": d["statuses"],
+           "cg_iterations_per_traj": d["cg_iterations_per_traj"],
+           "roofline": d["roofline"], "clocks": d["clocks"],
+           "loop_of_single_chain_launches": d["loop_of_single_chain_launches"]}
+    if "cpu_baseline" in d:
+        out["cpu_baseline"] = {k: d["cpu_baseline"][k] for k in ("value", "unit", "cores", "kind")
+                               if k in d["cpu_baseline"]}
+    return out
 
 
 def run_brs(args):

@@ -44,6 +44,7 @@ struct TcCtx {
     // (plain remainder) over bhi / blo with boxes of sk_nn(ns) rows
     CUtensorMap map_shi, map_slo;
     int sk_C_apply, sk_ns_apply;
+    float* inv_sk;       // per (target slice, K range) inverse scales [Nt][C]
     CUtensorMap map_skb_hi, map_skb_lo;
 };
 
@@ -439,6 +440,61 @@ __global__ void __launch_bounds__(NTHR, 1)
     tc_teardown(st);
 }
 
+// B operand of a standalone split-K application, one block per (target
+// slice t, K range r of the clusters' C CTAs): the source u of slice t
+// (in_{t+1} for M^dag, e^{i phi_{t-1}} in_{t-1} for M) over the range's
+// sites, scaled by 2^e with the largest |Re u|, |Im u| of the range in
+// [2^14, 2^15), split into FP16 hi and plain remainder lo in rows 2t (re)
+// and 2t + 1 (im); inv[t * C + r] = 2^-e (the consumer unscales its
+// partial per column with it: the scale is uniform over its K range).  Also
+// the FP32 phase table of slice t over the range.  One element per thread;
+// one pass over memory.
+constexpr int kSplitSkThreads = 256;   // >= the largest K range (4 chunks of 64)
+template <bool DAG>
+__global__ void __launch_bounds__(kSplitSkThreads)
+    k_split_sk(const double* __restrict__ phi, const float2* __restrict__ in,
+               float2* __restrict__ cis_f, __half* __restrict__ bhi, __half* __restrict__ blo,
+               float* __restrict__ inv, int V, int Vp, int Nt, int C) {
+    __shared__ float s_max[kSplitSkThreads / 32];
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const int t = blockIdx.x, r = blockIdx.y;
+    const int KS = (V + 15) / 16;
+    const int k0 = 16 * (KS * r / C), k1 = min(16 * (KS * (r + 1) / C), V);
+    const int ts = DAG ? (t + 1 == Nt ? 0 : t + 1) : (t == 0 ? Nt - 1 : t - 1);
+    const int k = k0 + (int)threadIdx.x;
+    float2 u = make_float2(0.f, 0.f);
+    if (k < k1) {
+        float sn, cs;
+        sincosf((float)phi[(size_t)t * V + k], &sn, &cs);
+        cis_f[(size_t)t * V + k] = make_float2(cs, sn);
+        u = in[(size_t)ts * V + k];
+        if (!DAG) {
+            sincosf((float)phi[(size_t)ts * V + k], &sn, &cs);
+            u = make_float2(cs * u.x - sn * u.y, cs * u.y + sn * u.x);
+        }
+    }
+    float mx = fmaxf(fabsf(u.x), fabsf(u.y));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    float m = 0.f;
+    for (int w = 0; w < kSplitSkThreads / 32; ++w) m = fmaxf(m, s_max[w]);
+    const int bits = __float_as_int(m), ex = (bits >> 23) & 0xff;
+    int e = 0;
+    if (bits > 0 && ex != 0xff) e = max(-120, min(120, 14 - (ex - 127)));
+    if (threadIdx.x == 0) inv[t * C + r] = __int_as_float((127 - e) << 23);
+    if (k < k1) {
+        const float sc = __int_as_float((127 + e) << 23);
+        const float x = u.x * sc, y = u.y * sc;
+        const __half h0 = __float2half_rn(x), h1 = __float2half_rn(y);
+        bhi[(size_t)(2 * t) * Vp + k] = h0;
+        bhi[(size_t)(2 * t + 1) * Vp + k] = h1;
+        blo[(size_t)(2 * t) * Vp + k] = __float2half_rn(x - __half2float(h0));
+        blo[(size_t)(2 * t + 1) * Vp + k] = __float2half_rn(y - __half2float(h1));
+    }
+}
+
 // Standalone application on split-K tiles (operand_mode 5): clusters of C
 // CTAs, cluster (ib, ng) = site block ib x n-group ng of ns target slices;
 // each CTA loads its 128 rows x K range of the scaled split of E by TMA
@@ -490,8 +546,8 @@ __global__ void __launch_bounds__(NTHR, 1)
         }
     }
     Team none = {};
-    SkEpiOut<DAG> epi{in, out, c.cis_f, inv, c.e_inv, c.V, c.Nt};
-    sk_finish<true>(st, g, none, c.V, 1.f, epi);
+    SkEpiOut<DAG> epi{in, out, c.cis_f, c.V, c.Nt};
+    sk_finish<true>(st, g, none, c.V, c.e_inv, epi, inv, c.Nt);
     cluster_barrier_all();   // the partials stay until every member has read them
     tc_teardown(st);
 }
@@ -1674,6 +1730,8 @@ int tc_ctx_init(hmc_ctx* c) {
                 return HMC_ERR_CUDA;
             c->tc->sk_C_apply = skC;
             c->tc->sk_ns_apply = skns;
+            c->tc->inv_sk = (float*)dev_alloc(c, (size_t)v.Nt * skC * sizeof(float), &okb);
+            if (!okb) return HMC_ERR_CUDA;
             // the CG's sources: r and u with their halo rows, boxes of ns rows,
             // and their FP16 splits, boxes of sk_nn(ns) rows
             const int rows16 = 2 * (v.Nt + 2);
@@ -1767,17 +1825,18 @@ int tc_apply(hmc_ctx* c, const double* phi, const float2* in, float2* out, bool 
     if (c->params.operand_mode == 5 && t->sk_C_apply > 0) {
         int C = t->sk_C_apply, ns = t->sk_ns_apply;
         const int grid = (v.Vr / tc::TM) * ((v.Nt + ns - 1) / ns) * C;
+        const dim3 sgrid(v.Nt, C);
         if (dag)
-            tc::k_split<true, true><<<v.Nt, tc::kSplitThreads, split_smem, s>>>(
-                phi, in, v.cis_f, t->bhi, t->blo, t->inv_col, v.V, v.Vp, v.Nt);
+            tc::k_split_sk<true><<<sgrid, tc::kSplitSkThreads, 0, s>>>(
+                phi, in, v.cis_f, t->bhi, t->blo, t->inv_sk, v.V, v.Vp, v.Nt, C);
         else
-            tc::k_split<false, true><<<v.Nt, tc::kSplitThreads, split_smem, s>>>(
-                phi, in, v.cis_f, t->bhi, t->blo, t->inv_col, v.V, v.Vp, v.Nt);
+            tc::k_split_sk<false><<<sgrid, tc::kSplitSkThreads, 0, s>>>(
+                phi, in, v.cis_f, t->bhi, t->blo, t->inv_sk, v.V, v.Vp, v.Nt, C);
         if (cudaGetLastError() != cudaSuccess) return HMC_ERR_CUDA;
         ChainView vv = v;
         const float2* inp = in;
         float2* outp = out;
-        const float* invp = t->inv_col;
+        const float* invp = t->inv_sk;
         void* args[] = {&t->map_shi, &t->map_slo, &t->map_skb_hi, &t->map_skb_lo, &vv,
                         &C, &ns, &inp, &outp, &invp};
         return launch_dependent(

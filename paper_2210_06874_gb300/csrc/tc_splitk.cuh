@@ -709,8 +709,11 @@ __device__ __forceinline__ void sk_issue_b16(TcState& st, const SkGeom& g, const
 // After the MMAs are issued: wait for the accumulator and stage it in
 // shared memory as FP32 columns [column][128 rows], multiplied by
 // stage_scale (the inverse of this CTA's operand scale, exact: a power of
-// two).  All threads; false if the wait failed (status set).
-__device__ __forceinline__ bool sk_stage(TcState& st, const SkGeom& g, float stage_scale) {
+// two), or, with col_inv, by the inverse scale of the column's slice and
+// this CTA's K range, col_inv[(t0 + column / 2) * C + rank] (standalone
+// applications).  All threads; false if the wait failed (status set).
+__device__ __forceinline__ bool sk_stage(TcState& st, const SkGeom& g, float stage_scale,
+                                         const float* col_inv = nullptr, int Nt = 0) {
     TileBars& bars = *st.bars;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t tmem = bars.tmem_base;
@@ -732,8 +735,14 @@ __device__ __forceinline__ bool sk_stage(TcState& st, const SkGeom& g, float sta
             tmem_ld16(tl + (uint32_t)(cb * 16), m);
             tmem_ld16(tl + (uint32_t)(Nn + cb * 16), l);
 #pragma unroll
-            for (int e = 0; e < 16; ++e)
-                stg[(cb * 16 + e) * TM + row] = (m[e] + l[e]) * stage_scale;
+            for (int e = 0; e < 16; ++e) {
+                float sc = stage_scale;
+                if (col_inv) {
+                    const int t = g.t0 + ((cb * 16 + e) >> 1);
+                    sc = t < Nt ? col_inv[t * g.C + g.rank] : 0.f;
+                }
+                stg[(cb * 16 + e) * TM + row] = (m[e] + l[e]) * sc;
+            }
         }
     }
     fence_before_sync();
@@ -809,8 +818,9 @@ __device__ __forceinline__ bool sk_reduce(const TcState& st, const SkGeom& g, Te
 
 template <bool HW, class Epi>
 __device__ __forceinline__ bool sk_finish(TcState& st, const SkGeom& g, Team& tcl, int V,
-                                          float unscale, Epi& epi) {
-    const bool ok = sk_stage(st, g, 1.f);
+                                          float unscale, Epi& epi, const float* col_inv = nullptr,
+                                          int Nt = 0) {
+    const bool ok = sk_stage(st, g, 1.f, col_inv, Nt);
     if constexpr (HW) {
         // every thread reaches the hardware cluster barrier, failed or not
         const bool r = sk_reduce<true>(st, g, tcl, V, unscale, epi);
@@ -963,7 +973,8 @@ struct SkEpiM {
 };
 
 // Epilogue of a standalone application at (t, i .. i+3): with
-// w = (E u)_t unscaled by the source slice's inverse scale inv[t] 2^-eE,
+// w = (E u)_t (the staged partials already unscaled by their operand
+// scales; the sum times 2^-eE),
 //     M:      out_t = in_t - s_t w                      (s_0 = -1)
 //     M^dag:  out_t = in_t - s_{t+1} e^{-i phi_t} w     (s_Nt = -1)
 template <bool DAG>
@@ -971,8 +982,6 @@ struct SkEpiOut {
     const float2* in;
     float2* out;
     const float2* cis;   // FP32 e^{i phi} (M^dag)
-    const float* inv;    // per target slice
-    float e_inv;
     int V, Nt;
     float4 c0, c1;
     __device__ __forceinline__ void prefetch(int t, int i) {
@@ -991,7 +1000,6 @@ struct SkEpiOut {
     }
     __device__ __forceinline__ void store(int t, int i, int, const float2 (&w)[4]) {
         const size_t o = (size_t)t * V + i;
-        const float u = inv[t] * e_inv;
         const float sg = DAG ? ((t == Nt - 1) ? -1.f : 1.f) : ((t == 0) ? -1.f : 1.f);
         const float2 ph[4] = {make_float2(c0.x, c0.y), make_float2(c0.z, c0.w),
                               make_float2(c1.x, c1.y), make_float2(c1.z, c1.w)};
@@ -1010,7 +1018,7 @@ struct SkEpiOut {
         float2 r[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            float2 wv = make_float2(w[e].x * u, w[e].y * u);
+            float2 wv = w[e];
             if (DAG) wv = cmulcf(ph[e], wv);
             r[e] = make_float2(a[e].x - sg * wv.x, a[e].y - sg * wv.y);
         }

@@ -150,7 +150,7 @@ def tune(params, iters=40, reps=2, single_cta=False, seed=1, team=0):
 _ru_cache = {}
 
 
-def tune_ru(params, candidates=(0.01, 0.05, 0.2), seed=2):
+def tune_ru(params, candidates=(0.003, 0.01, 0.05, 0.2), seed=2):
     """Return a copy of params with the reliable-update threshold ru_delta
     that solves fastest to params.cg_tol, timed with full mixed solves in
     the params' launch shape (the best value depends on the chain: fewer

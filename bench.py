@@ -831,7 +831,7 @@ def run_ours(args):
                     name, prec, min(args.cpu_sample_s, 10.0), phi_np=phi_np,
                     integrator=args.integrator, n_md=params.n_md)
     if world == 1 and name == "l24_nt96" and prec == "mixed" and not args.no_batch_line:
-        # the spec comparison on the batched workload, in the same line
+        # the batched workload against the plain FP64 GPU path, in the same line
         line["batch256"] = batch_summary(args)
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -88,9 +88,13 @@ def candidates(params, num_sms, single_cta=False):
         if V >= 128:
             # split-K tiles with E resident, clusters of C CTAs (the launch
             # takes as many clusters as fit; shapes the library refuses are
-            # skipped)
-            for C in (2, 4, 6, 8):
-                out.append((0, C, 0, 5))
+            # skipped); n-groups of the default size (at most 64 slices) or
+            # of 32 or 16 slices (more clusters share a small lattice)
+            for ns in (0, 32, 16):
+                if ns and ns >= Nt:
+                    continue
+                for C in (2, 4, 6, 8):
+                    out.append((0, C, ns, 5))
     return sorted(set(out))
 
 

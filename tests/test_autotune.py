@@ -16,9 +16,13 @@ def test_candidates_cover_one_cta_and_tile_teams():
                       (1, 1, 32, 1)]
     big = autotune.candidates(hmc.Params(L=24, Nt=96, beta=12.0), num_sms=148)
     assert all(mode in (1, 4, 5) for *_, mode in big)  # E rows too large to stay resident
-    # split-K tiles: clusters of 2..8 CTAs, the launch size left to the library
-    assert [s for s in big if s[3] == 5] == [(0, 2, 0, 5), (0, 4, 0, 5), (0, 6, 0, 5),
-                                             (0, 8, 0, 5)]
+    # split-K tiles: clusters of 2..8 CTAs, n-groups of the library's size or
+    # of 32 or 16 slices, the launch size left to the library
+    assert sorted(s for s in big if s[3] == 5) == sorted(
+        (0, C, ns, 5) for C in (2, 4, 6, 8) for ns in (0, 16, 32))
+    small_nt = autotune.candidates(hmc.Params(L=12, Nt=16, beta=2.0), num_sms=148)
+    assert sorted(s for s in small_nt if s[3] == 5) == sorted(
+        (0, C, 0, 5) for C in (2, 4, 6, 8))            # n-groups smaller than Nt only
     assert (0, 6, 0, 5) not in autotune.candidates(hmc.Params(L=6, Nt=32, beta=4.0),
                                                    num_sms=148, single_cta=True)
 

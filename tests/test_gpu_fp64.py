@@ -68,9 +68,16 @@ def test_apply_M_and_Mdag_fp64(L, Nt):
     phi = synth.gaussian_field(L * 100 + Nt, Nt, V, beta / Nt * U)
     psi = synth.complex_gaussian(L * 1000 + Nt, Nt, V)
     got = c.apply_M(t64(phi), t64(psi)).cpu().numpy()
-    assert rel(got, ops.apply_M(E, phi, psi)) < 1e-13
+    want = ops.apply_M(E, phi, psi)
+    assert rel(got, want) < 1e-13
+    # element by element: relative to the element plus the vector's RMS
+    rms = np.sqrt(np.mean(np.abs(want) ** 2))
+    assert np.all(np.abs(got - want) <= 1e-13 * (np.abs(want) + rms))
     got = c.apply_Mdag(t64(phi), t64(psi)).cpu().numpy()
-    assert rel(got, ops.apply_Mdag(E, phi, psi)) < 1e-13
+    want = ops.apply_Mdag(E, phi, psi)
+    assert rel(got, want) < 1e-13
+    rms = np.sqrt(np.mean(np.abs(want) ** 2))
+    assert np.all(np.abs(got - want) <= 1e-13 * (np.abs(want) + rms))
 
 
 def test_apply_full_size_l24_nt96():

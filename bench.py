@@ -647,7 +647,8 @@ def run_ours(args):
     if prec == "mixed" and not args.no_tune:
         from paper_2210_06874_gb300 import autotune
         if args.operand_mode is None:
-            params = autotune.tune(params)
+            # mass preconditioning on the mixed path runs on split-K tiles
+            params = autotune.tune(params, modes=(5,) if args.hb_inner > 0 else None)
         params = autotune.tune_ru(params)
         tuned = {"team_ctas": params.team_ctas, "inner_ctas": params.inner_ctas,
                  "tile_slices": params.tile_slices, "operand_mode": params.operand_mode,

@@ -150,9 +150,11 @@ typedef struct hmc_params {
                             and Weingarten, Nucl. Phys. B 380 (1992) 665): n_md
                             outer steps for the ratio force, hb_inner inner
                             steps per outer step for the bosonic and heavy
-                            forces.  The same target density.  FP64 precision
-                            only (HMC_ERR_UNSUPPORTED otherwise); integrator
-                            must be 0 */
+                            forces.  The same target density.  FP64, or mixed
+                            precision with operand_mode 5 (split-K tiles, whose
+                            epilogues scale the contraction by g; other mixed
+                            operand modes return HMC_ERR_UNSUPPORTED); every
+                            solve starts from zero; integrator must be 0 */
 } hmc_params;
 
 typedef struct hmc_cg_stats {

@@ -103,11 +103,13 @@ def pick(timings):
     return min(timings, key=lambda kv: (kv[1],) + tuple(kv[0]))[0]
 
 
-def tune(params, iters=40, reps=2, single_cta=False, seed=1, team=0):
+def tune(params, iters=40, reps=2, single_cta=False, seed=1, team=0, modes=None):
     """Return a copy of params with team_ctas, inner_ctas, tile_slices and
     operand_mode set to the fastest measured shape (team > 1: among the
-    shapes of a cluster team of that many CTAs)."""
-    key = (params.L, params.Nt, round(params.beta / params.Nt, 12), single_cta, team)
+    shapes of a cluster team of that many CTAs; modes: only those operand
+    modes, e.g. (5,) for mass preconditioning on the mixed path)."""
+    key = (params.L, params.Nt, round(params.beta / params.Nt, 12), single_cta, team,
+           tuple(modes) if modes else None)
     if key in _cache:
         (team_c, inner, ns, mode), _ = _cache[key]
     else:
@@ -121,6 +123,8 @@ def tune(params, iters=40, reps=2, single_cta=False, seed=1, team=0):
         timings = []
         shapes = team_candidates(params, team) if team > 1 else candidates(params, num_sms,
                                                                              single_cta)
+        if modes:
+            shapes = [sh for sh in shapes if sh[3] in modes]
         for team_c, inner, ns, mode in shapes:
             p = hmc.Params(**{**params.__dict__, "team_ctas": team_c, "inner_ctas": inner,
                               "tile_slices": ns, "operand_mode": mode,
@@ -192,7 +196,7 @@ def tune_ru(params, candidates=(0.003, 0.01, 0.05, 0.2), seed=2):
 def seconds_per_iteration(params, single_cta=False, team=0):
     """Measured seconds per CG iteration of the shape tune() chose."""
     tune(params, single_cta=single_cta, team=team)
-    key = (params.L, params.Nt, round(params.beta / params.Nt, 12), single_cta, team)
+    key = (params.L, params.Nt, round(params.beta / params.Nt, 12), single_cta, team, None)
     return _cache[key][1]
 
 

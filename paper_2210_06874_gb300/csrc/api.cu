@@ -369,7 +369,10 @@ int hmc_trajectory(hmc_ctx* c, double* phi, uint64_t seed, uint64_t traj_index, 
     a.integrator = c->params.integrator;
     a.hb_gamma = c->params.hb_gamma;
     a.hb_inner = c->params.hb_inner;
-    if (a.hb_inner > 0 && c->params.precision != HMC_PREC_FP64) return HMC_ERR_UNSUPPORTED;
+    // mass preconditioning: FP64, or the mixed path on split-K tiles (whose
+    // epilogues carry the heavy operator's hop factor)
+    if (a.hb_inner > 0 && c->params.precision != HMC_PREC_FP64 && c->params.operand_mode != 5)
+        return HMC_ERR_UNSUPPORTED;
     int st;
     if (c->params.precision == HMC_PREC_FP64)
         st = launch_trajectory_f64(c->view, c->num_sms, a, s);

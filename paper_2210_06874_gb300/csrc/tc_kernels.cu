@@ -594,8 +594,9 @@ struct BatchCallArgs {
 
 // FP64 true residual of x64: r64 = chi - M (M^dag x64); returns |r64|^2.
 __device__ bool f64_residual(const ChainView& c, Team& tm, f64::Smem& sm, const double2* chi,
-                             double2* x64, double& rr) {
+                             double2* x64, double& rr, double gm1 = 0.0) {
     f64::EpiArgs ea = {};
+    ea.hop_m1 = gm1;   // M_g = 1 - g S E D with g = 1 + gm1 (mass preconditioning)
     f64::apply_team<true, f64::EPI_STORE>(c, tm, x64, c.q, ea, sm);
     if (!team_barrier(tm)) return false;
     ea.chi = chi;
@@ -690,7 +691,7 @@ __device__ __forceinline__ void cg_after_r(CgScalars& s, float rr_new) {
 __device__ __noinline__ int sk_segment(const ChainView& c, Team& ti, TcState& st,
                                        const PersistentArgs& pa, ClusterSync* ics,
                                        CgScalars& s_cg, bool refresh, bool first,
-                                       const float2* cisf, double2* x64) {
+                                       const float2* cisf, double2* x64, float hop) {
     int reason = kSegMaxIter;
     const SkGeom g = sk_geom(ti.rank, pa.sk_C, pa.ns_tile, c.V, c.Nt, c.Vr, c.Vp);
     Team tcl = ti;
@@ -824,7 +825,7 @@ __device__ __noinline__ int sk_segment(const ChainView& c, Team& ti, TcState& st
         const int pu = s_pe[1];
         SkEpiDag ed{ow, c.u_f, pu != kNoPe ? b16 + 2 * plane : nullptr, b16 + 3 * plane,
                     __int_as_float((127 + (pu != kNoPe ? pu : 0)) << 23), c.Vp,
-                    cisf, s_cg.beta, c.V, c.Nt, 0.f, 0.f};
+                    cisf, s_cg.beta, hop, c.V, c.Nt, 0.f, 0.f};
         if (!sk_reduce<false>(st, g, tcl, c.V, c.e_inv, ed)) return -1;
         if (threadIdx.x == 0) s_pw[1] = b16 ? pu : kNoPe;
         sk_post(ti, c.gslots, ++st.gseq, ed.acc, ed.mx);   // u ready, |q|^2
@@ -841,7 +842,7 @@ __device__ __noinline__ int sk_segment(const ChainView& c, Team& ti, TcState& st
         const int pr = s_pe[0];
         SkEpiM em{ow, rh, pr != kNoPe ? b16 : nullptr, b16 + plane,
                   __int_as_float((127 + (pr != kNoPe ? pr : 0)) << 23), c.Vp,
-                  s_cg.alpha, c.V, c.Nt, 0.f, 0.f};
+                  s_cg.alpha, hop, c.V, c.Nt, 0.f, 0.f};
         if (!sk_reduce<false>(st, g, tcl, c.V, c.e_inv, em)) return -1;
         if (threadIdx.x == 0) s_pw[0] = b16 ? pr : kNoPe;
         sk_post(ti, c.gslots, ++st.gseq, em.acc, em.mx);   // r ready, |r|^2
@@ -867,7 +868,13 @@ template <int KIND>
 __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& sm64,
                          const CUtensorMap* mhi, const CUtensorMap* mlo,
                          const PersistentArgs& pa, ClusterSync* ics, const double2* chi,
-                         double2* x64, MixedResult& res, bool warm = false) {
+                         double2* x64, MixedResult& res, bool warm = false, double gm1 = 0.0) {
+    // the heavy operator M_g of mass preconditioning (gm1 = g - 1 != 0) is
+    // built into the split-K tiles' epilogues only
+    if (gm1 != 0.0 && KIND != kKindSplitK) {
+        set_status(tm.status, HMC_ERR_UNSUPPORTED);
+        return false;
+    }
     constexpr bool SMALL = KIND == kKindSmall;
     float2 *rf = c.r_f, *pf = c.p_f, *pn = c.p2_f, *qf = c.q_f, *xf = c.x_f;
     const int inner_size = min(max(pa.inner, 1), tm.size);
@@ -901,7 +908,7 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
     double rr_true = chi2;
     const double2* r0 = chi;
     if (warm) {
-        if (!f64_residual(c, tm, sm64, chi, x64, rr_true)) return false;
+        if (!f64_residual(c, tm, sm64, chi, x64, rr_true, gm1)) return false;
         ++res.reliable_updates;
         if (!finite_d(rr_true)) {
             res.status = HMC_ERR_NONFINITE;
@@ -1054,7 +1061,8 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
                 seg[1] = s_cg.it;
             }
         } else if (KIND == kKindSplitK && in_inner) {
-            const int reason = sk_segment(c, ti, st, pa, ics, s_cg, refresh, sk_first, cisf, x64);
+            const int reason = sk_segment(c, ti, st, pa, ics, s_cg, refresh, sk_first, cisf, x64,
+                                          (float)(1.0 + gm1));
             if (reason < 0) return false;
             refresh = false;
             sk_first = false;
@@ -1122,7 +1130,7 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
         const int it = (int)seg[1];
         if (reason == kSegNonfinite) { res.status = HMC_ERR_NONFINITE; break; }
         // FP64 true residual on all CTAs
-        if (!f64_residual(c, tm, sm64, chi, x64, rr_true)) return false;
+        if (!f64_residual(c, tm, sm64, chi, x64, rr_true, gm1)) return false;
         ++res.reliable_updates;
         if (!finite_d(rr_true)) { res.status = HMC_ERR_NONFINITE; break; }
         if (rr_true <= stop) { conv = true; break; }
@@ -1151,7 +1159,7 @@ __device__ bool cg_mixed(const ChainView& c, Team& tm, TcState& st, f64::Smem& s
         // residual leaves M^dag x in q, as the reliable update does
         f64::CgResult r64;
         if (!f64::cg_solve(c, tm, chi, x64, pa.tol, max(1, pa.max_iter - res.iterations), r64,
-                           sm64, true))
+                           sm64, true, gm1))
             return false;
         res.fp64_iterations = r64.iterations;
         res.true_res = r64.true_res;
@@ -1370,6 +1378,188 @@ __device__ bool run_trajectory(const ChainView& c, Team& tm, TcState& st, f64::S
     return ok;
 }
 
+// One HMC trajectory with mass preconditioning (Hasenbusch 2001) and the
+// two-level nested leapfrog (Sexton and Weingarten 1992) on the mixed path:
+// the same steps as f64::k_trajectory_hb, with every solve the mixed CG
+// (FP32 iterations on the split-K tiles, whose epilogues scale the
+// contraction by g for the heavy operator M_g = 1 - g S E D; FP64 reliable
+// updates and true residuals of the same operator) and everything else in
+// FP64.  Each solve's final FP64 residual leaves q = (M_g or M)^dag x, from
+// which the forces are formed.  Every solve starts from zero.  Results in
+// c.scalars as the FP64 kernel's.
+template <int KIND>
+__device__ __noinline__ bool run_trajectory_hb(const ChainView& c, Team& tm, TcState& st,
+                                              f64::Smem& sm64,
+                                  const CUtensorMap* mhi, const CUtensorMap* mlo,
+                                  const PersistentArgs& pa, ClusterSync* ics,
+                                  const TrajArgs& a) {
+    double* phi = a.phi;
+    const double inv_dU = 1.0 / (c.delta * c.U);
+    const double rsqrt2 = 0.70710678118654752440;
+    const double gm1 = a.hb_gamma - 1.0;
+    // 1. heat bath: momenta, the two noise vectors (rho_1 from stream 3 in
+    // c.rho, rho_2 from the plain noise stream in c.xh), start energy
+    double h0[3] = {0.0, 0.0, 0.0};
+    HMC_TEAM_ELEMS(e, c, tm) {
+        const double2 zp = normal_pair(philox_draw(a.seed, kStreamMomentum, a.traj, a.chain, e));
+        const double2 z2 = normal_pair(philox_draw(a.seed, kStreamNoise, a.traj, a.chain, e));
+        const double2 z1 = normal_pair(philox_draw(a.seed, kStreamHeavy, a.traj, a.chain, e));
+        const double ph = phi[e];
+        c.pi[e] = zp.x;
+        const double2 r1 = make_double2(z1.x * rsqrt2, z1.y * rsqrt2);
+        const double2 r2 = make_double2(z2.x * rsqrt2, z2.y * rsqrt2);
+        c.rho[e] = r1;
+        c.xh[e] = r2;
+        c.phi_old[e] = ph;
+        double s, co;
+        sincos(ph, &s, &co);
+        c.cis[e] = make_double2(co, s);
+        c.cis_f[e] = make_float2((float)co, (float)s);
+        h0[0] += ph * ph;
+        h0[1] += r1.x * r1.x + r1.y * r1.y + r2.x * r2.x + r2.y * r2.y;
+        h0[2] += zp.x * zp.x;
+    }
+    if (!team_sum<3>(tm, h0)) return false;
+    const double H0 = 0.5 * h0[0] * inv_dU + h0[1] + 0.5 * h0[2];
+    int iters_in = 0, iters_out = 0, solves_in = 0, solves_out = 0, rus = 0, fp64_iters = 0;
+    int status = HMC_OK;
+    double max_res = 0.0;
+    auto record = [&](const MixedResult& r, bool outer) {
+        (outer ? iters_out : iters_in) += r.iterations;
+        ++(outer ? solves_out : solves_in);
+        rus += r.reliable_updates;
+        fp64_iters += r.fp64_iterations;
+        max_res = fmax(max_res, r.true_res);
+        if (r.status != HMC_OK && status == HMC_OK) status = r.status;
+    };
+    // 2. chi_1 = M_g rho_1; chi_2 = M_g^dag (M_g M_g^dag)^{-1} M rho_2
+    f64::EpiArgs eg = {};
+    eg.hop_m1 = gm1;
+    f64::EpiArgs e1 = {};
+    f64::apply_team<false, f64::EPI_STORE>(c, tm, c.rho, c.chi, eg, sm64);
+    f64::apply_team<false, f64::EPI_STORE>(c, tm, c.xh, c.phi2, e1, sm64);
+    if (!team_barrier(tm)) return false;
+    MixedResult res{};
+    if (!cg_mixed<KIND>(c, tm, st, sm64, mhi, mlo, pa, ics, c.phi2, c.x2, res, false, gm1))
+        return false;
+    record(res, false);
+    if (res.status == HMC_OK) {
+        HMC_TEAM_ELEMS(e, c, tm) c.chi2[e] = c.q[e];   // q = M_g^dag x_2 (final residual)
+    } else {
+        f64::apply_team<true, f64::EPI_STORE>(c, tm, c.x2, c.chi2, eg, sm64);
+    }
+    if (!team_barrier(tm)) return false;
+    // 3. nested leapfrog
+    const double ed = a.eps * c.delta;
+    const double h = 1.0 / a.hb_inner;
+    auto drift = [&](double cf) {
+        HMC_TEAM_ELEMS(e, c, tm) {
+            const double ph = fma(cf * ed, c.pi[e], phi[e]);
+            phi[e] = ph;
+            double s, co;
+            sincos(ph, &s, &co);
+            c.cis[e] = make_double2(co, s);
+            c.cis_f[e] = make_float2((float)co, (float)s);
+        }
+        return team_barrier(tm);
+    };
+    // bosonic and heavy forces: F_B + F_1 = phi/(delta U) + 2 Im(x_1 conj(M_g^dag x_1))
+    auto kick_inner = [&](double cf) {
+        MixedResult r{};
+        if (!cg_mixed<KIND>(c, tm, st, sm64, mhi, mlo, pa, ics, c.chi, c.x, r, false, gm1))
+            return false;
+        record(r, false);
+        const double k = cf * ed;
+        if (r.status == HMC_OK) {
+            HMC_TEAM_ELEMS(e, c, tm) {
+                const double2 xv = c.x[e], y = c.q[e];
+                c.pi[e] -= k * (phi[e] * inv_dU + 2.0 * (xv.y * y.x - xv.x * y.y));
+            }
+        } else {
+            f64::EpiArgs ef = {};
+            ef.hop_m1 = gm1;
+            ef.phi = phi;
+            ef.pi = c.pi;
+            ef.inv_dU = inv_dU;
+            ef.kick = k;
+            f64::apply_team<true, f64::EPI_FORCE>(c, tm, c.x, nullptr, ef, sm64);
+        }
+        return team_barrier(tm);
+    };
+    // ratio force: F_2 = 2 Im(x_2 conj(M^dag x_2)) - 2 Im(conj(M_g^dag x_2 - x_2) chi_2)
+    auto kick_outer = [&](double cf) {
+        f64::apply_team<false, f64::EPI_STORE>(c, tm, c.chi2, c.phi2, eg, sm64);   // M_g chi_2
+        if (!team_barrier(tm)) return false;
+        MixedResult r{};
+        if (!cg_mixed<KIND>(c, tm, st, sm64, mhi, mlo, pa, ics, c.phi2, c.x2, r, false, 0.0))
+            return false;
+        record(r, true);
+        const double k = cf * ed;
+        f64::EpiArgs ef = {};
+        ef.phi = phi;
+        ef.pi = c.pi;
+        ef.inv_dU = 0.0;          // the bosonic force sits on the inner level
+        ef.kick = k;
+        if (r.status == HMC_OK) {
+            HMC_TEAM_ELEMS(e, c, tm) {
+                const double2 xv = c.x2[e], y = c.q[e];
+                c.pi[e] -= k * (2.0 * (xv.y * y.x - xv.x * y.y));
+            }
+        } else {
+            f64::apply_team<true, f64::EPI_FORCE>(c, tm, c.x2, nullptr, ef, sm64);
+        }
+        if (!team_barrier(tm)) return false;
+        ef.hop_m1 = gm1;
+        ef.chi = c.chi2;
+        f64::apply_team<true, f64::EPI_RATIO>(c, tm, c.x2, nullptr, ef, sm64);
+        return team_barrier(tm);
+    };
+    if (!kick_outer(0.5)) return false;
+    for (int k = 0; k < a.n_md; ++k) {
+        for (int m = 0; m < a.hb_inner; ++m) {
+            if (!kick_inner(m == 0 ? 0.5 * h : h)) return false;
+            if (!drift(h)) return false;
+        }
+        if (!kick_inner(0.5 * h)) return false;
+        if (!kick_outer(k + 1 < a.n_md ? 1.0 : 0.5)) return false;
+    }
+    // 4. end energy (the last kick of each level was at the final field) and
+    // Metropolis
+    double h1[4] = {0.0, 0.0, 0.0, 0.0};
+    HMC_TEAM_ELEMS(e, c, tm) {
+        const double ph = phi[e], pv = c.pi[e];
+        const double2 c1 = c.chi[e], x1 = c.x[e], p2 = c.phi2[e], x2 = c.x2[e];
+        h1[0] += ph * ph;
+        h1[1] += c1.x * x1.x + c1.y * x1.y;
+        h1[2] += p2.x * x2.x + p2.y * x2.y;
+        h1[3] += pv * pv;
+    }
+    if (!team_sum<4>(tm, h1)) return false;
+    const double H1 = 0.5 * h1[0] * inv_dU + h1[1] + h1[2] + 0.5 * h1[3];
+    const double dH = H1 - H0;
+    const double u = uniform_pair(philox_draw(a.seed, kStreamMetropolis, a.traj, a.chain, 0)).x;
+    const bool accept = u < exp(-dH);
+    if (!accept) {
+        HMC_TEAM_ELEMS(e, c, tm) phi[e] = c.phi_old[e];
+    }
+    if (tm.rank == 0 && threadIdx.x == 0) {
+        c.scalars[kTrajDH] = dH;
+        c.scalars[kTrajH0] = H0;
+        c.scalars[kTrajH1] = H1;
+        c.scalars[kTrajU] = u;
+        c.scalars[kTrajAccept] = accept ? 1.0 : 0.0;
+        c.scalars[kTrajIters] = iters_in + iters_out;
+        c.scalars[kTrajSolves] = solves_in + solves_out;
+        c.scalars[kTrajRU] = rus;
+        c.scalars[kTrajMaxRes] = max_res;
+        c.scalars[kTrajStatus] = status;
+        c.scalars[kTrajFp64Iters] = fp64_iters;
+        c.scalars[kTrajItersOuter] = iters_out;
+        c.scalars[kTrajSolvesOuter] = solves_out;
+    }
+    return true;
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(NTHR, 1)
     k_trajectory(const __grid_constant__ CUtensorMap mhi,
@@ -1382,7 +1572,16 @@ __global__ void __launch_bounds__(NTHR, 1)
     __shared__ ClusterSync s_cs;
     Team tm = make_team(c);
     cluster_begin(pa, &s_cs, c.status);
-    run_trajectory<KIND>(c, tm, st, sm64, &mhi, &mlo, pa, &s_cs, a);
+    if constexpr (KIND == kKindSplitK) {
+        // (mass preconditioning: split-K tiles only; the host refuses it for
+        // the other kinds)
+        if (a.hb_inner > 0)
+            run_trajectory_hb<KIND>(c, tm, st, sm64, &mhi, &mlo, pa, &s_cs, a);
+        else
+            run_trajectory<KIND>(c, tm, st, sm64, &mhi, &mlo, pa, &s_cs, a);
+    } else {
+        run_trajectory<KIND>(c, tm, st, sm64, &mhi, &mlo, pa, &s_cs, a);
+    }
     persistent_teardown<KIND == kKindSmall>(st);
     if (pa.cluster > 1) cluster_barrier_all();   // no member leaves while others may push
 }

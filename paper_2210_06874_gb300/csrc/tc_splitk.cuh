@@ -870,7 +870,8 @@ struct SkOwner {
 
 // M^dag epilogue of the split-K CG iteration at (t, i .. i+3): with
 // w = E r_{t+1},  G = w + beta G,  p' = r + beta p,
-// q = p' - s_{t+1} e^{-i phi_t} G,  u = e^{i phi_t} q.  Updates G, p (= p'),
+// q = p' - g s_{t+1} e^{-i phi_t} G,  u = e^{i phi_t} q (g = hop: 1 for M,
+// the hop factor of the heavy operator M_g).  Updates G, p (= p'),
 // q in shared memory and writes u to global memory; sums |q|^2.
 struct SkEpiDag {
     SkOwner ow;
@@ -880,6 +881,7 @@ struct SkEpiDag {
     int Vp;
     const float2* cis;
     float beta;
+    float hop;       // g of the operator 1 - g S E D (1 for M itself)
     int V, Nt;
     float acc;       // |q|^2 of the owned elements
     float mx;        // largest |Re|, |Im| of the u written
@@ -908,7 +910,8 @@ struct SkEpiDag {
             const float2 gv = make_float2(fmaf(beta, g0.x, w[e].x), fmaf(beta, g0.y, w[e].y));
             const float2 pv = make_float2(fmaf(beta, p0.x, rv.x), fmaf(beta, p0.y, rv.y));
             const float2 cg = cmulcf(ph[e], gv);
-            const float2 qv = make_float2(pv.x - sg * cg.x, pv.y - sg * cg.y);
+            const float sh = sg * hop;
+            const float2 qv = make_float2(pv.x - sh * cg.x, pv.y - sh * cg.y);
             ow.G[oi + e] = gv;
             ow.p[oi + e] = pv;
             ow.q[oi + e] = qv;
@@ -929,7 +932,7 @@ struct SkEpiDag {
 };
 
 // M epilogue of the split-K CG iteration at (t, i .. i+3): with
-// w = E u_{t-1},  Mq = q - s_t w,  x += alpha p,  r -= alpha Mq.  Updates x
+// w = E u_{t-1},  Mq = q - g s_t w,  x += alpha p,  r -= alpha Mq.  Updates x
 // and r in shared memory, writes r to global memory; sums |r|^2.
 struct SkEpiM {
     SkOwner ow;
@@ -938,12 +941,13 @@ struct SkEpiM {
     float bscale;
     int Vp;
     float alpha;
+    float hop;       // g of the operator 1 - g S E D (1 for M itself)
     int V, Nt;
     float acc;       // |r|^2 of the owned elements
     float mx;        // largest |Re|, |Im| of the r written
     __device__ __forceinline__ void prefetch(int, int) {}
     __device__ __forceinline__ void store(int t, int i, int oi, const float2 (&w)[4]) {
-        const float sg = (t == 0) ? -1.f : 1.f;
+        const float sg = (t == 0) ? -hop : hop;
         float2 rs[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {

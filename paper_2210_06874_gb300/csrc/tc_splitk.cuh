@@ -228,6 +228,16 @@ __device__ __forceinline__ bool sk_word_is(unsigned long long w, unsigned seq) {
     return (unsigned)(w >> 40) == (seq & 0xffffffu);
 }
 
+// Release store / acquire load of a team word at GPU scope.
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // Bounded polling: every 16th probe checks the team status and the time.
 __device__ __forceinline__ bool sk_poll_expired(const Team& ti, unsigned k, uint64_t& t0) {
     if ((k & 15u) != 0) return false;
@@ -264,9 +274,9 @@ __device__ inline void sk_post(const Team& ti, unsigned long long* slots, unsign
             m = fmaxf(m, s_m[w]);
         }
         const unsigned mexp = (__float_as_uint(m) >> 23) & 0xffu;
-        __threadfence();
-        *reinterpret_cast<volatile unsigned long long*>(slots + sk_slot(seq, ti.rank)) =
-            sk_word(seq, mexp, a);
+        // release: the block's writes (ordered before by the barrier above)
+        // become visible with the word
+        st_release_u64(slots + sk_slot(seq, ti.rank), sk_word(seq, mexp, a));
     }
 }
 
@@ -306,8 +316,9 @@ __device__ inline int sk_owner_list(const SkGeom& g, int V, int Nt, bool dag, in
 }
 
 // Warp 0: wait (bounded) until the n ranks in `list` have posted seq and
-// return the largest max exponent among them; the lanes that saw a post
-// fence (acquire) before the block barrier that the caller runs next.
+// return the largest max exponent among them; each lane reads its owner's
+// word with acquire semantics, and the block barrier that the caller runs
+// next orders the other threads after those reads.
 // `mexp` starts from `own_mexp` (0 when the list covers every owner).
 __device__ inline bool sk_wait_owners(const Team& ti, const unsigned long long* slots,
                                       unsigned seq, const int* list, int n, unsigned own_mexp,
@@ -316,17 +327,16 @@ __device__ inline bool sk_wait_owners(const Team& ti, const unsigned long long* 
     bool ok = true;
     unsigned m = own_mexp;
     for (int q = lane; q < n && ok; q += 32) {
-        const volatile unsigned long long* p = slots + sk_slot(seq, list[q]);
-        unsigned long long w = *p;
+        const unsigned long long* p = slots + sk_slot(seq, list[q]);
+        unsigned long long w = ld_acquire_u64(p);
         uint64_t t0 = 0;
         for (unsigned k = 1; !sk_word_is(w, seq); ++k) {
             if (sk_poll_expired(ti, k, t0)) { ok = false; break; }
             __nanosleep(32);
-            w = *p;
+            w = ld_acquire_u64(p);
         }
         m = max(m, (unsigned)(w >> 32) & 0xffu);
     }
-    __threadfence();
     ok = __all_sync(0xffffffffu, ok);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -559,6 +569,9 @@ __device__ __forceinline__ void sk_issue_source(const TcState& st, const SkGeom&
                                                 const CUtensorMap* map, int row0) {
     if (threadIdx.x != 0) return;
     fence_proxy_async();
+    // the owners' generic writes (acquired through their words) before this
+    // thread's async-proxy reads of them
+    asm volatile("fence.proxy.async.global;" ::: "memory");
     const uint32_t cb = 2u * (uint32_t)g.Nn * 128u;
     const uint32_t bytes = (uint32_t)KCH * (uint32_t)g.ns * 8u;
     for (int j = 0; j < g.nch; ++j) {
@@ -688,6 +701,7 @@ __device__ __forceinline__ void sk_issue_b16(TcState& st, const SkGeom& g, const
     const uint32_t phase = st.nskb & 1u;
     st.nskb += 1;
     if (threadIdx.x != 0) return;
+    asm volatile("fence.proxy.async.global;" ::: "memory");   // as sk_issue_source
     const uint32_t cb = 2u * (uint32_t)g.Nn * 128u;
     for (int j = 0; j < g.nch; ++j) {
         const uint32_t bar = smem_u32(&st.bars->skb[j]);

@@ -500,8 +500,9 @@ __global__ void __launch_bounds__(kSplitSkThreads)
 // each CTA loads its 128 rows x K range of the scaled split of E by TMA
 // (before waiting for the split pre-pass, which it does not read), then the
 // pre-split source rows 2 t0 .. 2 t0 + Nn of its K range (plain FP16 hi and
-// lo, one power-of-two scale per target slice), one barrier per 64-wide K
-// chunk, and issues each chunk's MMAs as it lands.  The C partials of a
+// lo, one power-of-two scale per target slice and K range), one barrier per
+// 64-wide K chunk, and issues each chunk's MMAs as it lands; it stages its
+// partial unscaled per column by its own range's scales.  The C partials of a
 // cluster are summed through distributed shared memory in rank order by the
 // owners of the outputs (deterministic); a last cluster barrier keeps every
 // member's shared memory alive until the others have read it.  E moves

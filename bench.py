@@ -240,6 +240,27 @@ def flush_l2(buf, acc):
     buf.fill_(1.0)
     torch.sum(buf, dim=0, out=acc)
 
+def e2e_host_calls(torch, stream, dev_in, dev_out, call, n):
+    """End to end through the C ABI with host buffers: n times, copy the
+    input from pinned host memory to the device, call, copy the output back
+    to pinned host memory; returns (ms per call, bytes in, bytes out)."""
+    h_in = torch.empty(dev_in.shape, dtype=dev_in.dtype, pin_memory=True)
+    h_in.copy_(dev_in.cpu())
+    h_out = torch.empty(dev_out.shape, dtype=dev_out.dtype, pin_memory=True)
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    for _ in range(n):
+        dev_in.copy_(h_in, non_blocking=True)
+        call()
+        h_out.copy_(dev_out, non_blocking=True)
+    e.record(stream)
+    e.synchronize()
+    nb_in = dev_in.numel() * dev_in.element_size()
+    nb_out = dev_out.numel() * dev_out.element_size()
+    return s.elapsed_time(e) / n, nb_in, nb_out
+
+
 def applies_per_traj(out, n_md):
     """M / M^dag applications in one trajectory: chi = M rho, two per CG
     iteration, two per FP64 true-residual check (one per solve and one per
@@ -907,6 +928,8 @@ def run_apply(args):
     e.record(stream)
     e.synchronize()
     eager_ms = s.elapsed_time(e) / args.applies
+    e2e_ms, e2e_in, e2e_out = e2e_host_calls(
+        torch, stream, psi, out, lambda: ctx.apply_M(phi, psi, out, prec=p), args.applies)
     n = args.steps * args.applies
     per_ms = total_ms / n
     flop = flops_per_apply(V, Nt)
@@ -939,6 +962,10 @@ def run_apply(args):
                        "timing": "one CUDA-graph replay of the step's C-ABI calls",
                        "l2": "flushed (256 MB write + read sweep) between timed steps"},
             "per_call_from_python_us": eager_ms * 1e3,
+            "e2e": {"value": 1e3 / e2e_ms, "unit": "M-applications/s",
+                    "h2d_bytes_per_step": e2e_in, "d2h_bytes_per_step": e2e_out,
+                    "how": "per call: psi from pinned host memory in, hmc_apply_M, the "
+                           "result back (the field phi stays on the device)"},
             "gpu_launches": n * 2 if prec != "fp64" else n * 2,
             "roofline": roof, "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1003,6 +1030,13 @@ def run_cg(args):
     clk = clocks.stop()
     ms_it = statistics.median(per_it)
     n64 = max(8, n_long // 20)
+    # end to end: chi from pinned host memory in, the long solve, x back
+    xbuf = torch.empty_like(chi)
+
+    def long_solve():
+        ctx.cg_solve(phi, chi, tol=1e-300, max_iter=n_long, prec=hmc.PREC_MIXED, x=xbuf,
+                     allow_not_converged=True)
+    e2e_ms, e2e_in, e2e_out = e2e_host_calls(torch, stream, chi, xbuf, long_solve, 1)
     ms64 = (solve_ms(hmc.PREC_FP64, 2 * n64) - solve_ms(hmc.PREC_FP64, n64)) / n64
     peaks, kind = load_peaks()
     flop = 2 * flops_per_apply(V, Nt)
@@ -1026,6 +1060,11 @@ def run_cg(args):
                        "l2": "flushed (256 MB write + read sweep) before every solve"},
             "us_per_cg_iteration": 1e3 * ms_it,
             "fp64_us_per_cg_iteration": 1e3 * ms64,
+            "e2e": {"value": 2e3 * n_long / e2e_ms, "unit": "M-applications/s",
+                    "h2d_bytes_per_step": e2e_in, "d2h_bytes_per_step": e2e_out,
+                    "how": "one solve of the longer length with chi in from pinned host "
+                           "memory and x back (its FP64 set-up and final residual "
+                           "included, unlike the value)"},
             "gpu_launches": 2 * args.steps,
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak,
@@ -1338,6 +1377,9 @@ def run_brs(args):
             times.append(s.elapsed_time(e))
     clk = clocks.stop()
     per_ms = statistics.median(times)
+    e2e_ms, e2e_in, e2e_out = e2e_host_calls(
+        torch, stream, psi, out, lambda: hmc.apply_brs(L, Nt, beta / Nt * kappa, cis, psi, out),
+        args.applies)
     bpe = 48.0 if prec == "fp64" else 24.0
     byts = bpe * N
     peaks, kind = load_peaks()
@@ -1352,6 +1394,10 @@ def run_brs(args):
                        "V": V, "Nt": Nt, "applies_per_step": args.applies,
                        "l2": "flushed (256 MB write + read sweep) before every application; median"},
             "gpu_launches": args.steps * args.applies,
+            "e2e": {"value": 1e3 / e2e_ms, "unit": "M-applications/s",
+                    "h2d_bytes_per_step": e2e_in, "d2h_bytes_per_step": e2e_out,
+                    "how": "per call: psi from pinned host memory in, hmc_apply_brs, the "
+                           "result back (the phase table stays on the device)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": None,
                          "algorithmic_bytes_per_apply": byts,

@@ -18,6 +18,7 @@ N > 1 (torchrun): each rank advances its own chain (chain id = rank): weak
 scaling, no collective on the data path.  Prints one JSON line on rank 0.
 """
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -881,9 +882,6 @@ def run_apply(args):
     build_lib.build()
     name = args.workload
     w, params, prec = workload_params(name, args.precision)
-    if args.operand_mode is not None:
-        params.operand_mode = args.operand_mode
-    ctx = hmc.Context(params)
     V, Nt = params.V, params.Nt
     dev = torch.device("cuda", local_rank)
     phi = torch.from_numpy(synth.gaussian_field(w["seed"], Nt, V, w["beta"] / Nt * w["U"],
@@ -892,6 +890,43 @@ def run_apply(args):
     p = hmc.PREC_FP64 if prec == "fp64" else hmc.PREC_MIXED
     psi = torch.from_numpy(synth.complex_gaussian(w["seed"] + 1, Nt, V)).to(dev).to(dt)
     out = torch.empty_like(psi)
+    tried = {}
+    if args.operand_mode is not None:
+        params.operand_mode = args.operand_mode
+    elif prec == "mixed" and not args.no_tune:
+        # the standalone tile kinds (site-major 1, slice-major 4, split-K 5),
+        # each timed on a few applications before the timed region
+        best = None
+        for mode in (1, 4, 5):
+            try:
+                c = hmc.Context(dataclasses.replace(params, operand_mode=mode))
+            except hmc.HmcError:
+                continue
+            try:
+                for _ in range(3):
+                    c.apply_M(phi, psi, out, prec=p)
+                g0 = torch.cuda.CUDAGraph()
+                torch.cuda.synchronize()
+                with torch.cuda.graph(g0):
+                    for _ in range(10):
+                        c.apply_M(phi, psi, out, prec=p)
+                g0.replay()
+                s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s0.record()
+                g0.replay()
+                e0.record()
+                e0.synchronize()
+                tried[mode] = s0.elapsed_time(e0) / 10
+                del g0
+            except hmc.HmcError:
+                continue
+            finally:
+                c.close()
+            if best is None or tried[mode] < tried[best]:
+                best = mode
+        if best is not None:
+            params.operand_mode = best
+    ctx = hmc.Context(params)
     for _ in range(args.warmup):
         ctx.apply_M(phi, psi, out, prec=p)
     stream = torch.cuda.current_stream()
@@ -959,6 +994,8 @@ def run_apply(args):
             "config": {"workload": name, "mode": "apply", "precision": prec, "V": V, "Nt": Nt,
                        "applies_per_step": args.applies,
                        "operand_mode": params.operand_mode,
+                       "operand_modes_tried_ms_per_call": {str(k): v for k, v in tried.items()}
+                       or None,
                        "timing": "one CUDA-graph replay of the step's C-ABI calls",
                        "l2": "flushed (256 MB write + read sweep) between timed steps"},
             "per_call_from_python_us": eager_ms * 1e3,

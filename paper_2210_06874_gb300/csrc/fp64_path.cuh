@@ -20,6 +20,7 @@ constexpr int TI = 32;     // sites per tile (= lanes of a warp)
 constexpr int TT = 8;      // slices per tile (= warps of the CTA)
 constexpr int KC = 32;     // K chunk
 constexpr int NTHR = TI * TT;
+static_assert(NTHR == KC * TT && (KC * TI) % NTHR == 0, "FP64 tile: chunk loads per thread");
 
 struct Smem {
     double Et[KC][TI];     // Et[kk][ii] = E[k0+kk][i0+ii] = E[i0+ii][k0+kk]
@@ -67,30 +68,46 @@ __device__ double apply_tile(const ChainView& c, int tile, const double2* __rest
     const int ii = threadIdx.x & (TI - 1), tt = threadIdx.x / TI;
     const double* __restrict__ E = c.E;
     const double2* __restrict__ cis = c.cis;
-    double ar = 0.0, ai = 0.0;
-    for (int k0 = 0; k0 < V; k0 += KC) {
+    // Chunk k0's E block and source values are loaded into registers while
+    // the previous chunk is contracted from shared memory (one buffer: the
+    // registers are the second stage), so the L2 latency of a chunk hides
+    // behind the FP64 arithmetic of the one before.  The summation order is
+    // that of a plain loop over k.
+    constexpr int kEPer = KC * TI / NTHR;   // E elements per thread and chunk
+    const int ukk = threadIdx.x % KC, us = threadIdx.x / KC;
+    double ev[kEPer];
+    double2 uv;
+    auto fetch = [&](int k0) {
 #pragma unroll
-        for (int e = threadIdx.x; e < KC * TI; e += NTHR) {
+        for (int j = 0; j < kEPer; ++j) {
+            const int e = threadIdx.x + j * NTHR;
             const int kk = e / TI, cc = e % TI;
             const int k = k0 + kk, i = i0 + cc;
-            sm.Et[kk][cc] = (k < V && i < V) ? E[(size_t)k * V + i] : 0.0;
+            ev[j] = (k < V && i < V) ? E[(size_t)k * V + i] : 0.0;
         }
-        {
-            const int kk = threadIdx.x % KC, s = threadIdx.x / KC;
-            const int k = k0 + kk, tq = t0 + s;
-            double2 u = make_double2(0.0, 0.0);
-            if (k < V && tq < Nt) {
-                if (DAG) {
-                    const int ts = (tq + 1 == Nt) ? 0 : tq + 1;
-                    u = in[(size_t)ts * V + k];
-                } else {
-                    const int ts = (tq == 0) ? Nt - 1 : tq - 1;
-                    u = cmul(cis[(size_t)ts * V + k], in[(size_t)ts * V + k]);
-                }
+        const int k = k0 + ukk, tq = t0 + us;
+        uv = make_double2(0.0, 0.0);
+        if (k < V && tq < Nt) {
+            if (DAG) {
+                const int ts = (tq + 1 == Nt) ? 0 : tq + 1;
+                uv = in[(size_t)ts * V + k];
+            } else {
+                const int ts = (tq == 0) ? Nt - 1 : tq - 1;
+                uv = cmul(cis[(size_t)ts * V + k], in[(size_t)ts * V + k]);
             }
-            sm.U[s][kk] = u;
         }
+    };
+    double ar = 0.0, ai = 0.0;
+    fetch(0);
+    for (int k0 = 0; k0 < V; k0 += KC) {
+#pragma unroll
+        for (int j = 0; j < kEPer; ++j) {
+            const int e = threadIdx.x + j * NTHR;
+            sm.Et[e / TI][e % TI] = ev[j];
+        }
+        sm.U[us][ukk] = uv;
         __syncthreads();
+        if (k0 + KC < V) fetch(k0 + KC);
 #pragma unroll 8
         for (int kk = 0; kk < KC; ++kk) {
             const double e = sm.Et[kk][ii];

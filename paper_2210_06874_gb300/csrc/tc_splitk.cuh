@@ -144,53 +144,6 @@ __device__ inline bool sk_load_E(TcState& st, const SkGeom& g, const CUtensorMap
     return ok;
 }
 
-// Source of the B operand: FP32 vector, or (refresh) the FP64 residual.
-struct SkSrc {
-    const float2* f;
-    const double2* d;
-    bool use_d;
-    int V;
-    __device__ __forceinline__ float2 one(size_t o) const {
-        if (use_d) {
-            const double2 a = d[o];
-            return make_float2((float)a.x, (float)a.y);
-        }
-        return f[o];
-    }
-    __device__ __forceinline__ void load8(int ts, int kb, float2 (&v)[8]) const {
-        const size_t o = (size_t)ts * V + kb;
-        if (use_d || kb + 8 > V) {
-#pragma unroll
-            for (int e = 0; e < 8; ++e)
-                v[e] = kb + e < V ? one(o + e) : make_float2(0.f, 0.f);
-            return;
-        }
-        const float4* s4 = reinterpret_cast<const float4*>(f + o);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const float4 a = s4[e];
-            v[2 * e] = make_float2(a.x, a.y);
-            v[2 * e + 1] = make_float2(a.z, a.w);
-        }
-    }
-};
-
-// FP16 split with a plain remainder, 8 values packed per uint4.
-__device__ __forceinline__ void split8_plain(const float (&x)[8], uint4& hi, uint4& lo) {
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const __half h0 = __float2half_rn(x[2 * e]);
-        const __half h1 = __float2half_rn(x[2 * e + 1]);
-        const __half l0 = __float2half_rn(x[2 * e] - __half2float(h0));
-        const __half l1 = __float2half_rn(x[2 * e + 1] - __half2float(h1));
-        h[e] = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
-        l[e] = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
-    }
-    hi = make_uint4(h[0], h[1], h[2], h[3]);
-    lo = make_uint4(l[0], l[1], l[2], l[3]);
-}
-
 // Bounded barrier over the CTAs of this cluster (release / acquire at
 // cluster scope): the members' shared-memory writes before it are visible
 // to every member's reads after it.  All threads.
@@ -408,41 +361,6 @@ __device__ __forceinline__ void sk_scale(unsigned mexp, float& scale, float& inv
 // nsl * 8 <= 512 items, so at most two per thread.
 constexpr int kSkItems = 2;
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
-                 "r"(src_bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// Scale, split and store one B item (slice tt, group grp) into a chunk.
-__device__ __forceinline__ void sk_store_item(const float4 (&v)[4], float scale, int Nn, int tt,
-                                              int grp, uint8_t* chunk) {
-    float re[8], im[8];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        re[2 * e] = v[e].x * scale;
-        im[2 * e] = v[e].y * scale;
-        re[2 * e + 1] = v[e].z * scale;
-        im[2 * e + 1] = v[e].w * scale;
-    }
-    uint4 hr, lr, hm, lm;
-    split8_plain(re, hr, lr);
-    split8_plain(im, hm, lm);
-    const int jr = 2 * tt, ji = jr + 1;
-    uint8_t* lo = chunk + (size_t)Nn * 128;
-    *reinterpret_cast<uint4*>(chunk + jr * 128 + ((grp ^ (jr & 7)) << 4)) = hr;
-    *reinterpret_cast<uint4*>(lo + jr * 128 + ((grp ^ (jr & 7)) << 4)) = lr;
-    *reinterpret_cast<uint4*>(chunk + ji * 128 + ((grp ^ (ji & 7)) << 4)) = hm;
-    *reinterpret_cast<uint4*>(lo + ji * 128 + ((grp ^ (ji & 7)) << 4)) = lm;
-}
-
 // Thread 0: the MMAs of chunk j (the CTA's K steps 4j .. 4j+3 within its
 // range); the last chunk commits the accumulator barrier.
 __device__ __forceinline__ void sk_issue_chunk(const TcState& st, const SkGeom& g, int j,
@@ -462,105 +380,6 @@ __device__ __forceinline__ void sk_issue_chunk(const TcState& st, const SkGeom& 
     if (j == g.nch - 1) mma_commit(smem_u32(&st.bars->acc_full));
 }
 
-// Build the stacked B of every chunk and issue the chunks' MMAs.  FP32
-// source: every thread first issues cp.async copies of its 16-byte pieces
-// of all chunks (raw layout [tt][64 sites] in the space of B chunk j; sites
-// past V copy zeros, pieces past the K range are skipped), one commit group
-// per chunk; then chunk by chunk it waits for the group, reads its items,
-// and after a block barrier writes them split in place.  (Measured at
-// L = 24: 5.5 us per application against 8.5 us with one bulk copy per
-// slice row on the TMA engine.)  FP64 source (the residual after a reliable
-// update): direct loads, chunk by chunk.
-template <bool DAG>
-__device__ __forceinline__ void sk_build_and_issue(const TcState& st, const SkGeom& g,
-                                                   const SkSrc& src, int Nt, float scale,
-                                                   uint32_t tmem) {
-    const int Nn = g.Nn;
-    uint8_t* bbase = st.base + g.b_off;
-    const uint32_t chunk_bytes = 2u * (uint32_t)Nn * 128u;
-    const int per_chunk = g.nsl * 8;
-    const int kend = 16 * g.ks1;
-    const int V = src.V;
-    if (!src.use_d) {
-        const int pieces = g.nsl * 32;   // 16-byte pieces (two sites) per chunk
-#pragma unroll
-        for (int j = 0; j < kSkMaxChunks; ++j) {
-            if (j < g.nch) {
-                const uint32_t raw = smem_u32(bbase + (size_t)j * chunk_bytes);
-                for (int pc = threadIdx.x; pc < pieces; pc += blockDim.x) {
-                    const int tt = pc >> 5, k = 16 * g.ks0 + KCH * j + 2 * (pc & 31);
-                    if (k >= kend) continue;
-                    const int ts = source_slice<DAG>(g.t0 + tt, Nt);
-                    const bool in = k < V;     // V is even: a pair never straddles V
-                    const float2* gp = src.f + (size_t)ts * V + (in ? k : 0);
-                    cp_async16(raw + (uint32_t)pc * 16u, gp, in ? 16u : 0u);
-                }
-            }
-            cp_async_commit();
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < kSkMaxChunks; ++j) {
-        if (j < g.nch) {
-            uint8_t* ch = bbase + (size_t)j * chunk_bytes;
-            float4 v[kSkItems][4];
-            if (!src.use_d) {
-                // the copies of chunks 0..j are complete for this thread
-                if (j == 0) cp_async_wait<kSkMaxChunks - 1>();
-                else if (j == 1) cp_async_wait<kSkMaxChunks - 2>();
-                else if (j == 2) cp_async_wait<kSkMaxChunks - 3>();
-                else cp_async_wait<0>();
-                __syncthreads();
-                const float4* raw = reinterpret_cast<const float4*>(ch);
-#pragma unroll
-                for (int m = 0; m < kSkItems; ++m) {
-                    const int r = threadIdx.x + m * NTHR;
-                    if (r < per_chunk) {
-                        // item (tt, grp): 8 sites = 4 pieces of raw row tt
-                        const int tt = r >> 3, grp = r & 7;
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) v[m][e] = raw[tt * 32 + grp * 4 + e];
-                    }
-                }
-                __syncthreads();   // every read of the raw chunk before the split overwrites it
-            } else {
-#pragma unroll
-                for (int m = 0; m < kSkItems; ++m) {
-                    const int r = threadIdx.x + m * NTHR;
-                    const int kb = 16 * g.ks0 + KCH * j + 8 * (r & 7);
-                    if (r < per_chunk && kb < kend) {
-                        const int ts = source_slice<DAG>(g.t0 + (r >> 3), Nt);
-                        const size_t o = (size_t)ts * V + kb;
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const float2 a =
-                                kb + 2 * e < V ? src.one(o + 2 * e) : make_float2(0.f, 0.f);
-                            const float2 b = kb + 2 * e + 1 < V ? src.one(o + 2 * e + 1)
-                                                                : make_float2(0.f, 0.f);
-                            v[m][e] = make_float4(a.x, a.y, b.x, b.y);
-                        }
-                    }
-                }
-            }
-#pragma unroll
-            for (int m = 0; m < kSkItems; ++m) {
-                const int r = threadIdx.x + m * NTHR;
-                const int kb = 16 * g.ks0 + KCH * j + 8 * (r & 7);
-                if (r < per_chunk && kb < kend) sk_store_item(v[m], scale, Nn, r >> 3, r & 7, ch);
-            }
-            fence_proxy_async();
-            __syncthreads();
-            if (threadIdx.x == 0) sk_issue_chunk(st, g, j, smem_u32(ch), tmem);
-        }
-    }
-}
-
-// One split-K application: B from src (the source of every target slice of
-// the n-group: t+1 for M^dag, t-1 for M) scaled by `scale`, the MMAs, the
-// partial accumulator staged, a cluster sync, then this CTA's owned
-// outputs: epi.store(tt, i, ow, w) gets w[4] = (E u)(i .. i+3) of slice
-// t0 + tt (unscaled by 1/scale * 2^-eE), ow = the owner index of site i.
-// All threads call it; false if a bounded wait failed (status set).
 // Split-K CG source by TMA (thread 0): for every chunk j of this CTA's K
 // range, the box of 64 sites from 16 ks0 + 64 j and ns rows from row0 of
 // the halo layout (zeros past V and past the last row) into the space of

@@ -1350,7 +1350,10 @@ def batch_summary(args):
     raised)."""
     import copy
     b_args = copy.copy(args)
-    b_args.steps, b_args.warmup, b_args.therm = 3, 1, None
+    # the standalone batched line's schedule (2 thermalisation trajectories
+    # and the bench's warm-up ones from a cold start, then 3 timed): the
+    # chains grow more expensive as they thermalise, so both report the same
+    b_args.steps, b_args.therm = 3, None
     b_args.cpu_sample_s = min(args.cpu_sample_s, 10.0)
     try:
         d = run_batch(b_args, emit=False)

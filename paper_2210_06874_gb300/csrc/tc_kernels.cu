@@ -1386,8 +1386,10 @@ __device__ bool run_trajectory(const ChainView& c, Team& tm, TcState& st, f64::S
 // contraction by g for the heavy operator M_g = 1 - g S E D; FP64 reliable
 // updates and true residuals of the same operator) and everything else in
 // FP64.  Each solve's final FP64 residual leaves q = (M_g or M)^dag x, from
-// which the forces are formed.  Every solve starts from zero.  Results in
-// c.scalars as the FP64 kernel's.
+// which the forces are formed.  The first solve of each level starts from
+// zero, the later ones from that level's previous solution (same right-hand
+// side on the inner level; consecutive solves of a level sit one step of
+// that level apart).  Results in c.scalars as the FP64 kernel's.
 template <int KIND>
 __device__ __noinline__ bool run_trajectory_hb(const ChainView& c, Team& tm, TcState& st,
                                               f64::Smem& sm64,
@@ -1465,10 +1467,12 @@ __device__ __noinline__ bool run_trajectory_hb(const ChainView& c, Team& tm, TcS
         return team_barrier(tm);
     };
     // bosonic and heavy forces: F_B + F_1 = phi/(delta U) + 2 Im(x_1 conj(M_g^dag x_1))
+    bool warm_in = false, warm_out = false;
     auto kick_inner = [&](double cf) {
         MixedResult r{};
-        if (!cg_mixed<KIND>(c, tm, st, sm64, mhi, mlo, pa, ics, c.chi, c.x, r, false, gm1))
+        if (!cg_mixed<KIND>(c, tm, st, sm64, mhi, mlo, pa, ics, c.chi, c.x, r, warm_in, gm1))
             return false;
+        warm_in = true;
         record(r, false);
         const double k = cf * ed;
         if (r.status == HMC_OK) {
@@ -1492,8 +1496,9 @@ __device__ __noinline__ bool run_trajectory_hb(const ChainView& c, Team& tm, TcS
         f64::apply_team<false, f64::EPI_STORE>(c, tm, c.chi2, c.phi2, eg, sm64);   // M_g chi_2
         if (!team_barrier(tm)) return false;
         MixedResult r{};
-        if (!cg_mixed<KIND>(c, tm, st, sm64, mhi, mlo, pa, ics, c.phi2, c.x2, r, false, 0.0))
+        if (!cg_mixed<KIND>(c, tm, st, sm64, mhi, mlo, pa, ics, c.phi2, c.x2, r, warm_out, 0.0))
             return false;
+        warm_out = true;
         record(r, true);
         const double k = cf * ed;
         f64::EpiArgs ef = {};

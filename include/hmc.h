@@ -153,8 +153,10 @@ typedef struct hmc_params {
                             forces.  The same target density.  FP64, or mixed
                             precision with operand_mode 5 (split-K tiles, whose
                             epilogues scale the contraction by g; other mixed
-                            operand modes return HMC_ERR_UNSUPPORTED); every
-                            solve starts from zero; integrator must be 0 */
+                            operand modes return HMC_ERR_UNSUPPORTED); FP64
+                            solves start from zero, mixed ones after the first
+                            of each level from that level's previous
+                            solution; integrator must be 0 */
 } hmc_params;
 
 typedef struct hmc_cg_stats {
